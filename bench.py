@@ -1,0 +1,418 @@
+"""Benchmark of the sliding-window-sum hot path on GB300.
+
+Workload (the configuration the headline metric is quoted on): the generic sliding-sum sweep
+over 2^28 elements -- int32 uniform in [-2^20, 2^20) for + mod 2^32, min, max, xor; affine maps
+(a, b) uniform uint32 (non-commutative composition); fp32 N(0,1) for +; windows
+w in {4, 16, 64, 256, 1024}.  One step = all 30 (operator, w) sliding sums, inputs resident in
+HBM.  Every input and output is larger than L2 (no flush needed).
+
+Printed: ONE JSON line with the whole-job GB/s (algorithmic bytes: input + output of every call),
+the roofline of the sliding-sum kernels against the measured HBM copy bandwidth, the same metric
+end to end (pinned host buffers, copies inside the timed region), the oracle timed on host cores
+on a bounded sample, secondary minimizer measurements, and the SM clocks seen while timing.
+
+``--impl reference`` times the oracle (the plain CPU statement of Eq. 2) instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OPS = ["add_i32", "min_i32", "max_i32", "xor_i32", "affine_u32", "add_f32"]
+WS = [4, 16, 64, 256, 1024]
+ESIZE = {"affine_u32": 8}
+METRIC = "minimizer Gbp/s & sliding-sum GB/s vs HBM peak; batched vs plain; p99 latency"
+WORKLOAD = ("sliding-sum sweep: 2^28 elements; int32 U[-2^20,2^20) for +,min,max,xor; affine (a,b) uint32; "
+            "fp32 N(0,1) for +; w in {4,16,64,256,1024}")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 28, help="elements per sliding-sum input")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, launched by torchrun for N > 1)
+# ------------------------------------------------------------------------------------------
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available() and args.impl == "ours":
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world <= 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def case_bytes(op: str, w: int, n: int) -> int:
+    es = ESIZE.get(op, 4)
+    return es * (n + (n - w + 1))
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def make_inputs(n: int, device, seed: int):
+    from paper_1811_10074_gb300 import synth
+    x32 = synth.int32_uniform(n, seed=seed, device=device)
+    xa = synth.affine_pairs(n, seed=seed, device=device)
+    xf = synth.f32_normal(n, seed=seed, device=device)
+    return {"add_i32": x32, "min_i32": x32, "max_i32": x32, "xor_i32": x32, "affine_u32": xa, "add_f32": xf}
+
+
+def cpu_baseline(n_sample: int, seed: int = 42):
+    """The oracle (plain O(wN) Eq. 2, single thread) on n_sample elements per case."""
+    import oracle
+    xs = make_inputs(n_sample, "cpu", seed)
+    total_bytes = 0
+    t0 = time.perf_counter()
+    for op in OPS:
+        for w in WS:
+            oracle.sliding_sum(op, w, xs[op])
+            total_bytes += case_bytes(op, w, n_sample)
+    dt = time.perf_counter() - t0
+    return total_bytes / dt / 1e9, dt
+
+
+def run_ours(args, world, rank, local):
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    xs = make_inputs(n, dev, seed=42 + rank)
+    outs = {}
+    for op in OPS:
+        x = xs[op]
+        outs[op] = torch.empty((n,) + tuple(x.shape[1:]), dtype=x.dtype, device=dev)
+    ctx = P.default_context(dev.index)
+    stream = torch.cuda.current_stream()
+    cases = [(op, w) for op in OPS for w in WS]
+    step_bytes = sum(case_bytes(op, w, n) for op, w in cases)
+
+    def step(events=None):
+        for i, (op, w) in enumerate(cases):
+            if events is not None:
+                events[i][0].record(stream)
+            P.sliding_sum(op, w, xs[op], out=outs[op][: n - w + 1], ctx=ctx, stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cases]
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    ms_total = max_over_ranks(world, ms_total)
+    ms_step = ms_total / args.steps
+    value = world * step_bytes / (ms_step / 1e3) / 1e9
+    ctx.sync()
+
+    # roofline of the sliding-sum kernels, per launch
+    per_case = {}
+    tot_b, tot_ms = 0, 0.0
+    for i, (op, w) in enumerate(cases):
+        d = [ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps)]
+        ms = sum(d) / len(d)
+        b = case_bytes(op, w, n)
+        per_case[f"{op}/w{w}"] = round(b / (ms / 1e3) / 1e9, 1)
+        tot_b += b * len(d)
+        tot_ms += sum(d)
+    peak, peak_kind = measured_peaks()
+    achieved = tot_b / (tot_ms / 1e3) / 1e9
+
+    # end to end through the public API with pinned host buffers
+    hx = {op: xs[op].cpu().pin_memory() for op in ("add_i32", "affine_u32", "add_f32")}
+    hx.update({"min_i32": hx["add_i32"], "max_i32": hx["add_i32"], "xor_i32": hx["add_i32"]})
+    hy = {op: torch.empty(outs[op].shape, dtype=outs[op].dtype).pin_memory() for op in OPS}
+    h2d = d2h = 0
+
+    def e2e_step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        for op in OPS:
+            xs[op].copy_(hx[op], non_blocking=True)
+            h2d += hx[op].numel() * hx[op].element_size()
+            for w in WS:
+                m = n - w + 1
+                P.sliding_sum(op, w, xs[op], out=outs[op][:m], ctx=ctx, stream=stream)
+                hy[op][:m].copy_(outs[op][:m], non_blocking=True)
+                d2h += hy[op][:m].numel() * hy[op].element_size()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e_ms = max_over_ranks(world, e_start.elapsed_time(e_end)) / args.steps
+    e2e_value = world * step_bytes / (e_ms / 1e3) / 1e9
+    del hx, hy
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32,u32x2,f32",
+        "data": "synthetic (SplitMix64 seed 42, generated on the device)",
+        "config": {"workload": WORKLOAD, "n": n, "ops": OPS, "w": WS, "calls_per_step": len(cases),
+                   "bytes_per_step": step_bytes, "l2": "inputs and outputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "k_slide_bc (block-combine sliding sum, all operators)", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "traffic": None, "per_case_gbs": per_case},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(e_ms, 3)},
+        "gpu_launches": len(cases) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1:
+        v, dt = cpu_baseline(args.cpu_sample)
+        result["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"{args.cpu_sample} elements per (op, w) case, all 30 cases, "
+                                            f"{dt:.1f} s single-threaded naive O(wN)"}
+    if not args.no_extras and rank == 0:
+        result["minimizers"] = minimizer_extras(dev, ctx)
+    del xs, outs
+    torch.cuda.empty_cache()
+    return result
+
+
+def time_call(fn, reps: int, stream):
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def minimizer_extras(dev, ctx):
+    """Secondary numbers: fused minimizers (Gbp/s) and the paper-equivalent sliding minimum over
+    precomputed hashes (GB/s vs HBM)."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    out = {}
+    peak, _ = measured_peaks()
+    # plain workload: 1,000,000 bases, k=15, w=10
+    n = 1_000_000
+    seq = synth.acgt_uniform_packed(n, seed=42, device=dev)
+    h, p, cnt = P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False)
+    ms = time_call(lambda: P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False), 50, stream)
+    out["plain_1e6"] = {"ms_per_call": round(ms, 4), "gbp_s": round(n / (ms / 1e3) / 1e9, 2),
+                        "picks": int(cnt.item()), "k": 15, "w": 10}
+    # long sequence: 2^31 uniform bases (k=15 w=10 and k=19 w=10)
+    n = 1 << 31
+    seq = synth.acgt_uniform_packed(n, seed=43, device=dev)
+    for k, w in ((15, 10), (19, 10), (15, 50)):
+        cap = int(n * 2.6 / (w + 1)) + 1024
+        ms = time_call(lambda: P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False), 3, stream)
+        _, _, cnt = P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
+        picks = int(cnt.item())
+        hb = 4 if 2 * k <= 32 else 8
+        bytes_ = n / 4 + picks * (hb + 4)
+        out[f"fused_2^31_k{k}_w{w}"] = {"ms": round(ms, 3), "gbp_s": round(n / (ms / 1e3) / 1e9, 1),
+                                        "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
+    del seq
+    torch.cuda.empty_cache()
+    # paper-equivalent: sliding minimum over 2^28 precomputed 30-bit hashes, w = 10
+    m = 1 << 28
+    keys = synth.uint32_hashes(m, device=dev)
+    cap = m // 4
+    ms = time_call(lambda: P.minimizers_from_keys(keys, 10, capacity=cap, ctx=ctx, stream=stream, sync=False), 5,
+                   stream)
+    _, _, cnt = P.minimizers_from_keys(keys, 10, capacity=cap, ctx=ctx, stream=stream, sync=False)
+    picks = int(cnt.item())
+    b = 4 * m + 8 * picks
+    out["sliding_min_keys_2^28_w10"] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
+                                        "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the oracle on host cores
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    import oracle
+    oracle.build()
+    ns = max(args.cpu_sample // 2, 1 << 12)
+    xs = make_inputs(ns, "cpu", 42)
+    cases = [(op, w) for op in OPS for w in WS]
+    step_bytes = sum(case_bytes(op, w, ns) for op, w in cases)
+
+    def step():
+        for op, w in cases:
+            oracle.sliding_sum(op, w, xs[op])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = step_bytes / dt / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32,u32x2,f32", "data": "synthetic (SplitMix64 seed 42)",
+        "config": {"workload": WORKLOAD, "n": ns, "sample": f"{ns} elements per case (bounded sample of 2^28)"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{ns} elements per (op, w) case, all 30 cases per step"},
+        "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    res = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

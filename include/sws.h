@@ -1,0 +1,146 @@
+/*
+ * sws.h -- C ABI of a GB300 (sm_103a) library for sliding window sums and the minimizer
+ * pipeline built on them, after R. Snytsar and Y. Turakhia, "Parallel approach to sliding
+ * window sums" (arXiv 1811.10074).
+ *
+ * General rules for every entry point:
+ *   - Data pointers are DEVICE pointers owned by the caller unless stated otherwise; the
+ *     library never frees or keeps them.  Outputs are preallocated by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *     are asynchronous on it: inputs must stay valid and outputs untouched until the stream
+ *     reaches the call.
+ *   - Every call returns an sws_status.  Nothing aborts, exits or traps.  Argument errors are
+ *     reported before any work is queued.  Faults found on the device (a bounded wait that ran
+ *     out) are recorded in the context and reported by sws_sync().
+ *   - A context owns the device workspace that some calls need (tile status words for ordered
+ *     output).  One context may be used from one host thread at a time; calls that use the
+ *     workspace must not overlap on the device (use one context per concurrent stream).
+ *   - Lengths are element counts (bases for DNA).  DNA is 2-bit packed: A=0 C=1 G=2 T=3, base
+ *     i in byte i>>2 at bits 2*(i&3); a sequence of n bases occupies ceil(n/4) bytes.
+ */
+#ifndef SWS_H
+#define SWS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status ------------------------------------------------------------------------------ */
+typedef int sws_status;
+#define SWS_OK 0
+#define SWS_ERR_INVALID 1     /* bad argument (message in sws_last_error)                   */
+#define SWS_ERR_OOM 2         /* the context workspace could not be grown                  */
+#define SWS_ERR_CAPACITY 3    /* more results than the caller's capacity (count still exact) */
+#define SWS_ERR_CUDA 4        /* a CUDA runtime call failed                                 */
+#define SWS_ERR_TIMEOUT 5     /* a bounded device-side wait ran out; results are invalid     */
+#define SWS_ERR_UNSUPPORTED 6 /* valid but outside what this build implements               */
+
+/* Thread-local description of the last error of this thread (never NULL). */
+const char *sws_last_error(void);
+
+/* ---- context ----------------------------------------------------------------------------- */
+typedef struct sws_ctx sws_ctx;
+
+/* Create a context on CUDA device `device` (made current on the calling thread). */
+sws_status sws_create(sws_ctx **out, int device);
+/* Destroy a context; waits for the device first.  NULL is accepted. */
+sws_status sws_destroy(sws_ctx *ctx);
+/* Grow the workspace to at least `bytes` now (so that later calls, e.g. under stream
+ * capture, allocate nothing).  Returns SWS_ERR_OOM if it cannot. */
+sws_status sws_reserve(sws_ctx *ctx, uint64_t bytes);
+/* Wait for `stream`, then report (and clear) any device-side fault recorded by this
+ * context's kernels: SWS_ERR_TIMEOUT if a bounded wait ran out. */
+sws_status sws_sync(sws_ctx *ctx, void *stream);
+
+/* ---- sliding window sum (Eq. 2, Sec. 2.2) ---------------------------------------------- */
+/* Operators.  Element layouts:
+ *   SWS_OP_ADD_I32    int32, addition mod 2^32
+ *   SWS_OP_MIN_I32    int32, signed minimum
+ *   SWS_OP_MAX_I32    int32, signed maximum
+ *   SWS_OP_XOR_I32    int32, bitwise xor
+ *   SWS_OP_AFFINE_U32 pair {uint32 a, uint32 b} (8 bytes) = map x -> a*x+b mod 2^32; the sum
+ *                     x_p (+) x_{p+1} is the map "apply x_p, then x_{p+1}" (not commutative)
+ *   SWS_OP_ADD_F32    float, addition (results are fp32; not bit-reproducible across variants) */
+#define SWS_OP_ADD_I32 0
+#define SWS_OP_MIN_I32 1
+#define SWS_OP_MAX_I32 2
+#define SWS_OP_XOR_I32 3
+#define SWS_OP_AFFINE_U32 4
+#define SWS_OP_ADD_F32 5
+
+/* Algorithm variants. */
+#define SWS_VARIANT_AUTO 0          /* tuned choice (see sws_tune)                              */
+#define SWS_VARIANT_BLOCK_COMBINE 1 /* blocks of w: in-block suffix + next-block prefix, O(1)/output */
+#define SWS_VARIANT_DOUBLING 2      /* ceil(log2 w) doubling levels, O(log w)/output            */
+#define SWS_VARIANT_PREFIX_DIFF 3   /* y_p = S_{p+w-1} - S_{p-1}; ADD_I32 and XOR_I32 only      */
+
+/* Eq. 2: out[p] = in[p] (+) in[p+1] (+) ... (+) in[p+w-1] for p = 0 .. n-w (n-w+1 outputs,
+ * exactly w addends each, Sec. 2.2).
+ *   in, out : device arrays of n and n-w+1 elements of the operator's type; must not overlap;
+ *             aligned to the element size (16-byte alignment enables vector access).
+ *   n < w   : writes nothing and returns SWS_OK.   w < 1 or an unknown op: SWS_ERR_INVALID.
+ * Uses no workspace. */
+sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *out, uint64_t n, int variant,
+                           void *stream);
+
+/* ---- k-mers (Sec. 2.4: a k-mer is the sliding sum of k bases under concatenation) --------- */
+#define SWS_KMER_FWD 0       /* r_i..r_{i+k-1} as a base-4 number, first base most significant  */
+#define SWS_KMER_RC 1        /* reverse complement of the same k bases                            */
+#define SWS_KMER_CANONICAL 2 /* min(FWD, RC)                                                      */
+#define SWS_KMER_HASH 3      /* Wang's 64-bit integer mix of CANONICAL, truncated to 2k bits after
+                                every step (a bijection on [0, 4^k))                              */
+
+/* Values of the n-k+1 k-mers of a packed sequence.  1 <= k <= 32.  out holds uint32 values
+ * when 2k <= 32, else uint64.  n < k writes nothing. */
+sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int kind, void *out, void *stream);
+
+/* ---- minimizers (Sec. 2.4) ---------------------------------------------------------------- */
+/* Keys a window's minimum is taken over (ties go to the leftmost k-mer, i.e. keys are
+ * ordered by (value, position)). */
+#define SWS_MINI_HASH 0      /* SWS_KMER_HASH values (the default; "hashed k-mers", Sec. 4)  */
+#define SWS_MINI_CANONICAL 1 /* canonical k-mers                                          */
+#define SWS_MINI_FWD 2       /* forward k-mers: lexicographic seeds as in the Fig. 2 example */
+
+/* Minimizers of one packed sequence of n bases (n < 2^32).
+ * For every window position p (w consecutive k-mers starting at p, Sec. 2.4) the least key
+ * and its position are found; consecutive windows with the same pick store it once.
+ *   nblocks   : device int64 pairs [start, end) of bases that are N, sorted and disjoint (may be
+ *               NULL when n_nblocks = 0).  A window touching an N base is dropped and each
+ *               N-free stretch is an independent sequence (no deduplication across N-blocks).
+ *   hash_out  : key values, uint32 when 2k <= 32 else uint64; pos_out: uint32 k-mer starts.
+ *               Picks come in increasing position.  At most `capacity` are written.
+ *   count_out : device uint64 receiving the exact number of picks (also when > capacity:
+ *               then only the first `capacity` picks are stored).
+ *   Limits: 1 <= k <= 32, 1 <= w <= 4000.  Uses workspace (8 bytes per 4032 windows). */
+sws_status sws_minimizers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                          const int64_t *nblocks, uint64_t n_nblocks, void *hash_out, uint32_t *pos_out,
+                          uint64_t capacity, uint64_t *count_out, void *stream);
+
+/* Paper-equivalent task of Sec. 4: deduplicated sliding minimum, with (value, position) keys,
+ * over a precomputed array of m uint32 key values (e.g. hashed 15-mers).  Outputs as for
+ * sws_minimizers (key_out uint32).  1 <= w <= 4000, m < 2^32. */
+sws_status sws_minimizers_from_keys(sws_ctx *ctx, const uint32_t *keys, uint64_t m, int w, uint32_t *key_out,
+                                    uint32_t *pos_out, uint64_t capacity, uint64_t *count_out, void *stream);
+
+/* Batched minimizers: nreads reads stored back to back in one packed stream, read r being
+ * bases [base_offsets[r], base_offsets[r+1]) (device int64 array of nreads+1 entries,
+ * non-decreasing, base_offsets[0] = 0, base_offsets[nreads] = total_bases, which is also passed
+ * by value; total_bases < 2^32).  Every read is an independent sequence (Sec. 2.4 applied per
+ * read); all reads are processed by one launch whose tiles span read boundaries.
+ *   hash_out/pos_out : picks of all reads, read by read; positions are read-local.
+ *   pick_offsets     : device uint64 [nreads+1]; read r's picks are
+ *                      [pick_offsets[r], pick_offsets[r+1]); pick_offsets[nreads] = total.
+ *   count_out        : device uint64, the exact total (only `capacity` picks are stored).
+ * Same limits as sws_minimizers.  Uses workspace. */
+sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t *base_offsets, uint64_t nreads,
+                                uint64_t total_bases, int k, int w, int mode, void *hash_out, uint32_t *pos_out,
+                                uint64_t capacity, uint64_t *pick_offsets, uint64_t *count_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWS_H */

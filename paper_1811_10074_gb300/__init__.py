@@ -1,1 +1,9 @@
-"""GB300-native sliding window sums and minimizers (arXiv 1811.10074)."""
+"""GB300-native sliding window sums and minimizers (arXiv 1811.10074).
+
+The computation lives in a CUDA library with a C ABI (``include/sws.h``); ``binding`` is its
+thin ctypes binding and ``synth`` the seeded input generators.  Importing the package does not
+load the library; the first call does, and raises if it has not been built.
+"""
+
+from .binding import (Context, SwsError, default_context, kmers, minimizers, minimizers_batch,  # noqa: F401
+                      minimizers_from_keys, sliding_sum)

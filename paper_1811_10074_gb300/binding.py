@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in ``include/sws.h``.
+
+Argument marshalling only: torch tensors supply device memory (``data_ptr()``) and the current
+CUDA stream; every step of the computation runs in the CUDA library.  If the library has not
+been built, every call raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+OPS = {"add_i32": 0, "min_i32": 1, "max_i32": 2, "xor_i32": 3, "affine_u32": 4, "add_f32": 5}
+VARIANTS = {"auto": 0, "block_combine": 1, "doubling": 2, "prefix_diff": 3}
+KMER_KINDS = {"fwd": 0, "rc": 1, "canonical": 2, "hash": 3}
+MINI_MODES = {"hash": 0, "canonical": 1, "fwd": 2}
+
+SWS_OK = 0
+SWS_ERR_CAPACITY = 3
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CAPACITY", 4: "CUDA", 5: "TIMEOUT", 6: "UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+vp = ctypes.c_void_p
+u64 = ctypes.c_uint64
+i32 = ctypes.c_int
+
+
+class SwsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sws error {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# name -> (restype, argtypes): every entry point of include/sws.h
+SIGNATURES = {
+    "sws_last_error": (ctypes.c_char_p, []),
+    "sws_create": (i32, [ctypes.POINTER(vp), i32]),
+    "sws_destroy": (i32, [vp]),
+    "sws_reserve": (i32, [vp, u64]),
+    "sws_sync": (i32, [vp, vp]),
+    "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
+    "sws_kmers": (i32, [vp, vp, u64, i32, i32, vp, vp]),
+    "sws_minimizers": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
+    "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
+    "sws_minimizers_batch": (i32, [vp, vp, vp, u64, u64, i32, i32, i32, vp, vp, u64, vp, vp, vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _build.LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"the CUDA library {p} is not built; run paper_1811_10074_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != SWS_OK:
+        raise SwsError(status, load().sws_last_error().decode())
+
+
+class Context:
+    """An sws context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = vp()
+        _check(load().sws_create(ctypes.byref(h), self.device))
+        self.handle = h
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            _lib.sws_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, nbytes: int):
+        _check(load().sws_reserve(self.handle, int(nbytes)))
+
+    def sync(self, stream=None):
+        _check(load().sws_sync(self.handle, _stream(stream)))
+
+
+def default_context(device: int | None = None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device()
+    with _lock:
+        c = _ctx.get(device)
+    if c is None:
+        c = Context(device)
+        with _lock:
+            _ctx[device] = c
+    return c
+
+
+def _stream(stream):
+    if stream is None:
+        return vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return vp(stream.cuda_stream)
+    return vp(int(stream))
+
+
+def _ptr(t):
+    return vp(t.data_ptr()) if t is not None else vp(0)
+
+
+def _dev(t: torch.Tensor, what: str):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
+# ------------------------------------------------------------------------------------------
+# Entry points
+# ------------------------------------------------------------------------------------------
+
+def sliding_sum(op: str, w: int, x: torch.Tensor, out: torch.Tensor | None = None, variant: str = "auto",
+                ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """Eq. 2 over ``x`` (int32 for the integer ops, float32 for add_f32, int32 [n, 2] for affine)."""
+    _dev(x, "x")
+    ctx = ctx or default_context(x.device.index)
+    n = x.shape[0]
+    m = max(n - w + 1, 0)
+    if out is None:
+        out = torch.empty((m,) + tuple(x.shape[1:]), dtype=x.dtype, device=x.device)
+    _dev(out, "out")
+    _check(load().sws_sliding_sum(ctx.handle, OPS[op], int(w), _ptr(x), _ptr(out), n, VARIANTS[variant],
+                                  _stream(stream)))
+    return out
+
+
+def kmers(seq: torch.Tensor, n: int, k: int, kind: str = "hash", out: torch.Tensor | None = None,
+          ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """k-mer values (int32 bit patterns when 2k <= 32, else int64)."""
+    _dev(seq, "seq")
+    ctx = ctx or default_context(seq.device.index)
+    m = max(n - k + 1, 0)
+    if out is None:
+        out = torch.empty(m, dtype=torch.int32 if 2 * k <= 32 else torch.int64, device=seq.device)
+    _check(load().sws_kmers(ctx.handle, _ptr(seq), int(n), int(k), KMER_KINDS[kind], _ptr(out), _stream(stream)))
+    return out
+
+
+def _trim(hash_out, pos_out, count, capacity, ctx, stream):
+    ctx.sync(stream)
+    c = int(count.item())
+    if c > capacity:
+        raise SwsError(SWS_ERR_CAPACITY, f"{c} picks exceed the capacity {capacity}")
+    return hash_out[:c], pos_out[:c], c
+
+
+def minimizers(seq: torch.Tensor, n: int, k: int, w: int, mode: str = "hash", nblocks: torch.Tensor | None = None,
+               capacity: int | None = None, ctx: Context | None = None, stream=None, sync: bool = True):
+    """(keys, positions) of the deduplicated minimizers; keys int32 bit patterns (2k <= 32) or int64.
+
+    With ``sync=False`` returns the untrimmed buffers and the device count tensor."""
+    _dev(seq, "seq")
+    ctx = ctx or default_context(seq.device.index)
+    dev = seq.device
+    nwin = max(n - (w + k - 1) + 1, 0)
+    if capacity is None:
+        capacity = nwin
+    h = torch.empty(max(capacity, 1), dtype=torch.int32 if 2 * k <= 32 else torch.int64, device=dev)
+    p = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    nb = 0
+    if nblocks is not None:
+        _dev(nblocks, "nblocks")
+        nb = nblocks.shape[0]
+    _check(load().sws_minimizers(ctx.handle, _ptr(seq), int(n), int(k), int(w), MINI_MODES[mode],
+                                 _ptr(nblocks) if nb else vp(0), nb, _ptr(h), _ptr(p), capacity, _ptr(cnt),
+                                 _stream(stream)))
+    if not sync:
+        return h, p, cnt
+    h, p, _ = _trim(h, p, cnt, capacity, ctx, stream)
+    return h, p
+
+
+def minimizers_from_keys(keys: torch.Tensor, w: int, capacity: int | None = None, ctx: Context | None = None,
+                         stream=None, sync: bool = True):
+    """Deduplicated sliding minimum (value, position) over a precomputed uint32 key array."""
+    _dev(keys, "keys")
+    ctx = ctx or default_context(keys.device.index)
+    m = keys.shape[0]
+    if capacity is None:
+        capacity = max(m - w + 1, 0)
+    h = torch.empty(max(capacity, 1), dtype=torch.int32, device=keys.device)
+    p = torch.empty(max(capacity, 1), dtype=torch.int32, device=keys.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=keys.device)
+    _check(load().sws_minimizers_from_keys(ctx.handle, _ptr(keys), m, int(w), _ptr(h), _ptr(p), capacity, _ptr(cnt),
+                                           _stream(stream)))
+    if not sync:
+        return h, p, cnt
+    h, p, _ = _trim(h, p, cnt, capacity, ctx, stream)
+    return h, p
+
+
+def minimizers_batch(seq: torch.Tensor, offsets: torch.Tensor, total_bases: int, k: int, w: int, mode: str = "hash",
+                     capacity: int | None = None, ctx: Context | None = None, stream=None, sync: bool = True):
+    """Per-read minimizers of reads stored back to back: (keys, read-local positions, pick offsets)."""
+    _dev(seq, "seq")
+    _dev(offsets, "offsets")
+    ctx = ctx or default_context(seq.device.index)
+    nreads = offsets.shape[0] - 1
+    if capacity is None:
+        capacity = max(int(total_bases), 1)
+    dev = seq.device
+    h = torch.empty(max(capacity, 1), dtype=torch.int32 if 2 * k <= 32 else torch.int64, device=dev)
+    p = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    po = torch.empty(nreads + 1, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    _check(load().sws_minimizers_batch(ctx.handle, _ptr(seq), _ptr(offsets), nreads, int(total_bases), int(k), int(w),
+                                       MINI_MODES[mode], _ptr(h), _ptr(p), capacity, _ptr(po), _ptr(cnt),
+                                       _stream(stream)))
+    if not sync:
+        return h, p, po, cnt
+    h, p, _ = _trim(h, p, cnt, capacity, ctx, stream)
+    return h, p, po

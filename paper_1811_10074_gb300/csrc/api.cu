@@ -1,0 +1,326 @@
+// api.cu -- the C ABI declared in include/sws.h: argument checks, the context and its device
+// workspace, and dispatch to the kernels.  Host code only.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/sws.h"
+#include "internal.h"
+
+struct sws_ctx {
+  int device = 0;
+  int *d_err = nullptr;      // device error word (DevErr bits)
+  void *ws = nullptr;        // workspace
+  uint64_t ws_size = 0;
+  int num_sms = 0;
+};
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+sws_status fail(sws_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+sws_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(SWS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SWS_CUDA(expr)                                 \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+sws_status enter(sws_ctx *ctx) {
+  if (!ctx) return fail(SWS_ERR_INVALID, "context is NULL");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return SWS_OK;
+}
+
+uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+// Make the workspace at least `bytes` long.  Growing waits for the device (the old buffer may
+// still be in use by queued work) and is refused while `stream` is being captured.
+sws_status ensure_ws(sws_ctx *ctx, uint64_t bytes, cudaStream_t stream) {
+  if (bytes <= ctx->ws_size) return SWS_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(SWS_ERR_OOM, "workspace must grow to %llu bytes during stream capture; call sws_reserve first",
+                (unsigned long long)bytes);
+  const uint64_t want = round_up(bytes + bytes / 4, 1 << 20);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_size = 0;
+  e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(SWS_ERR_OOM, "cannot allocate %llu bytes of workspace", (unsigned long long)want);
+  }
+  ctx->ws_size = want;
+  return SWS_OK;
+}
+
+int op_esize(int op) { return op == SWS_OP_AFFINE_U32 ? 8 : 4; }
+
+bool aligned_to(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Workspace of a minimizer launch: status words, a 256-byte slot for the tile counter, one
+// tile-barrier word per tile, then `extra` bytes.
+struct MiniWs {
+  uint64_t status_bytes, counter_off, tilebar_off, extra_off, total;
+};
+MiniWs mini_ws_layout(uint64_t num_tiles, uint64_t extra) {
+  MiniWs L;
+  L.status_bytes = round_up(num_tiles * 8, 256);
+  L.counter_off = L.status_bytes;
+  L.tilebar_off = L.counter_off + 256;
+  L.extra_off = L.tilebar_off + round_up(num_tiles * 8, 256);
+  L.total = L.extra_off + round_up(extra, 256);
+  return L;
+}
+
+sws_status check_mini_args(int k, int w, int mode) {
+  if (k < 1 || k > 32) return fail(SWS_ERR_INVALID, "k must be in [1, 32] (got %d)", k);
+  if (w < 1) return fail(SWS_ERR_INVALID, "w must be >= 1 (got %d)", w);
+  if (sws::mini_tile_windows(w) == 0) return fail(SWS_ERR_UNSUPPORTED, "w = %d exceeds the supported maximum", w);
+  if (mode < SWS_MINI_HASH || mode > SWS_MINI_FWD) return fail(SWS_ERR_INVALID, "unknown key mode %d", mode);
+  return SWS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sws_last_error(void) { return g_err.c_str(); }
+
+sws_status sws_create(sws_ctx **out, int device) {
+  if (!out) return fail(SWS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  SWS_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(SWS_ERR_INVALID, "device %d out of range (%d devices)", device, ndev);
+  SWS_CUDA(cudaSetDevice(device));
+  sws_ctx *c = new sws_ctx();
+  c->device = device;
+  cudaError_t e = cudaMalloc(&c->d_err, 256);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc(error word)");
+  }
+  e = cudaMemset(c->d_err, 0, 256);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    delete c;
+    return cuda_fail(e, "context setup");
+  }
+  *out = c;
+  return SWS_OK;
+}
+
+sws_status sws_destroy(sws_ctx *ctx) {
+  if (!ctx) return SWS_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return SWS_OK;
+}
+
+sws_status sws_reserve(sws_ctx *ctx, uint64_t bytes) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  return ensure_ws(ctx, bytes, nullptr);
+}
+
+sws_status sws_sync(sws_ctx *ctx, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  SWS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int err = 0;
+  SWS_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    SWS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    return fail(SWS_ERR_TIMEOUT, "a bounded device-side wait ran out (bits 0x%x); results of the affected calls are invalid",
+                err);
+  }
+  return SWS_OK;
+}
+
+sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *out, uint64_t n, int variant,
+                           void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (op < SWS_OP_ADD_I32 || op > SWS_OP_ADD_F32) return fail(SWS_ERR_INVALID, "unknown operator %d", op);
+  if (w < 1) return fail(SWS_ERR_INVALID, "w must be >= 1 (got %d)", w);
+  if (variant < SWS_VARIANT_AUTO || variant > SWS_VARIANT_PREFIX_DIFF)
+    return fail(SWS_ERR_INVALID, "unknown variant %d", variant);
+  if (n < (uint64_t)w) return SWS_OK;
+  if (!in || !out) return fail(SWS_ERR_INVALID, "in/out is NULL");
+  const int es = op_esize(op);
+  if (!aligned_to(in, es) || !aligned_to(out, es))
+    return fail(SWS_ERR_INVALID, "in/out must be aligned to the element size (%d bytes)", es);
+  {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in), b = reinterpret_cast<uintptr_t>(out);
+    const uintptr_t ae = a + n * (uint64_t)es, be = b + (n - w + 1) * (uint64_t)es;
+    if (a < be && b < ae) return fail(SWS_ERR_INVALID, "in and out overlap");
+  }
+  if (variant == SWS_VARIANT_PREFIX_DIFF && op != SWS_OP_ADD_I32 && op != SWS_OP_XOR_I32)
+    return fail(SWS_ERR_INVALID, "prefix-difference needs an invertible operator (ADD_I32 or XOR_I32)");
+  sws::SlideLaunch L;
+  L.op = op;
+  L.variant = variant == SWS_VARIANT_AUTO ? SWS_VARIANT_BLOCK_COMBINE : variant;
+  // the smaller tile when it keeps the halo re-read under a quarter of the tile
+  const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
+  L.cfg = (w - 1) * 4 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
+  if (sws::slide_tile_outputs(L.cfg, es, w) == 0)
+    return fail(SWS_ERR_UNSUPPORTED, "w = %d is larger than the tile of this build", w);
+  cudaError_t e = sws::launch_sliding_sum(L, in, out, n, w, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "sliding-sum launch");
+  return SWS_OK;
+}
+
+sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int kind, void *out, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (k < 1 || k > 32) return fail(SWS_ERR_INVALID, "k must be in [1, 32] (got %d)", k);
+  if (kind < SWS_KMER_FWD || kind > SWS_KMER_HASH) return fail(SWS_ERR_INVALID, "unknown k-mer kind %d", kind);
+  if (n < (uint64_t)k) return SWS_OK;
+  if (!seq || !out) return fail(SWS_ERR_INVALID, "seq/out is NULL");
+  if (!aligned_to(out, 2 * k <= 32 ? 4 : 8)) return fail(SWS_ERR_INVALID, "out is not aligned to its element size");
+  cudaError_t e = sws::launch_kmers(seq, n, k, kind, out, ctx->d_err, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "k-mer launch");
+  return SWS_OK;
+}
+
+static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq, const uint32_t *keys, uint64_t n,
+                                    int k, int w, int mode, const int64_t *nblocks, uint64_t n_nblocks,
+                                    void *hash_out, uint32_t *pos_out, uint64_t capacity, uint64_t *count_out,
+                                    void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  s = check_mini_args(k, w, mode);
+  if (s) return s;
+  if (!count_out) return fail(SWS_ERR_INVALID, "count_out is NULL");
+  if (capacity > 0 && (!hash_out || !pos_out)) return fail(SWS_ERR_INVALID, "hash_out/pos_out is NULL");
+  if (n >= (1ull << 32)) return fail(SWS_ERR_INVALID, "sequences must be shorter than 2^32");
+  if (n_nblocks > 0 && !nblocks) return fail(SWS_ERR_INVALID, "nblocks is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t span = source == sws::SRC_DNA ? (uint64_t)(w + k - 1) : (uint64_t)w;
+  const uint64_t nwin = n >= span ? n - span + 1 : 0;
+  const uint64_t tiles = sws::mini_num_tiles(nwin, w);
+  if (tiles == 0) {
+    SWS_CUDA(cudaMemsetAsync(count_out, 0, sizeof(uint64_t), st));
+    return SWS_OK;
+  }
+  if (source == sws::SRC_DNA && !seq) return fail(SWS_ERR_INVALID, "seq is NULL");
+  if (source == sws::SRC_KEYS && !keys) return fail(SWS_ERR_INVALID, "keys is NULL");
+  const MiniWs L = mini_ws_layout(tiles, 0);
+  s = ensure_ws(ctx, L.total, st);
+  if (s) return s;
+  char *ws = static_cast<char *>(ctx->ws);
+  SWS_CUDA(cudaMemsetAsync(ws, 0, L.tilebar_off, st));
+  sws::MiniArgs a{};
+  a.seq = seq;
+  a.keys = keys;
+  a.n = n;
+  a.k = source == sws::SRC_DNA ? k : 1;
+  a.w = w;
+  a.mode = mode;
+  a.bar = nblocks;
+  a.nbar = n_nblocks;
+  a.hash_out = hash_out;
+  a.pos_out = pos_out;
+  a.capacity = capacity;
+  a.count_out = count_out;
+  a.status = reinterpret_cast<unsigned long long *>(ws);
+  a.tile_counter = reinterpret_cast<unsigned int *>(ws + L.counter_off);
+  a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar_off);
+  a.err = ctx->d_err;
+  cudaError_t e = sws::launch_minimizers(a, source, sws::BAR_NBLOCK, tiles, st);
+  if (e != cudaSuccess) return cuda_fail(e, "minimizer launch");
+  return SWS_OK;
+}
+
+sws_status sws_minimizers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                          const int64_t *nblocks, uint64_t n_nblocks, void *hash_out, uint32_t *pos_out,
+                          uint64_t capacity, uint64_t *count_out, void *stream) {
+  return minimizers_common(ctx, sws::SRC_DNA, seq, nullptr, n, k, w, mode, nblocks, n_nblocks, hash_out, pos_out,
+                           capacity, count_out, stream);
+}
+
+sws_status sws_minimizers_from_keys(sws_ctx *ctx, const uint32_t *keys, uint64_t m, int w, uint32_t *key_out,
+                                    uint32_t *pos_out, uint64_t capacity, uint64_t *count_out, void *stream) {
+  return minimizers_common(ctx, sws::SRC_KEYS, nullptr, keys, m, 1, w, SWS_MINI_HASH, nullptr, 0, key_out, pos_out,
+                           capacity, count_out, stream);
+}
+
+sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t *base_offsets, uint64_t nreads,
+                                uint64_t total_bases, int k, int w, int mode, void *hash_out, uint32_t *pos_out,
+                                uint64_t capacity, uint64_t *pick_offsets, uint64_t *count_out, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  s = check_mini_args(k, w, mode);
+  if (s) return s;
+  if (!count_out || !pick_offsets) return fail(SWS_ERR_INVALID, "count_out/pick_offsets is NULL");
+  if (capacity > 0 && (!hash_out || !pos_out)) return fail(SWS_ERR_INVALID, "hash_out/pos_out is NULL");
+  if (nreads > 0 && !base_offsets) return fail(SWS_ERR_INVALID, "base_offsets is NULL");
+  if (total_bases >= (1ull << 32)) return fail(SWS_ERR_INVALID, "a batch must hold fewer than 2^32 bases");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t span = (uint64_t)(w + k - 1);
+  const uint64_t nwin = total_bases >= span ? total_bases - span + 1 : 0;
+  const uint64_t tiles = nreads > 0 ? sws::mini_num_tiles(nwin, w) : 0;
+  if (tiles == 0) {
+    SWS_CUDA(cudaMemsetAsync(count_out, 0, sizeof(uint64_t), st));
+    SWS_CUDA(cudaMemsetAsync(pick_offsets, 0, (nreads + 1) * sizeof(uint64_t), st));
+    return SWS_OK;
+  }
+  if (!seq) return fail(SWS_ERR_INVALID, "seq is NULL");
+  const uint64_t fix_blocks = (nreads + 1023) / 1024 + 1;
+  const MiniWs L = mini_ws_layout(tiles, fix_blocks * 8);
+  s = ensure_ws(ctx, L.total, st);
+  if (s) return s;
+  char *ws = static_cast<char *>(ctx->ws);
+  SWS_CUDA(cudaMemsetAsync(ws, 0, L.tilebar_off, st));
+  SWS_CUDA(cudaMemsetAsync(pick_offsets, 0xff, (nreads + 1) * sizeof(uint64_t), st));
+  sws::MiniArgs a{};
+  a.seq = seq;
+  a.n = total_bases;
+  a.k = k;
+  a.w = w;
+  a.mode = mode;
+  a.bar = base_offsets;
+  a.nbar = nreads;
+  a.hash_out = hash_out;
+  a.pos_out = pos_out;
+  a.capacity = capacity;
+  a.count_out = count_out;
+  a.pick_offsets = pick_offsets;
+  a.status = reinterpret_cast<unsigned long long *>(ws);
+  a.tile_counter = reinterpret_cast<unsigned int *>(ws + L.counter_off);
+  a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar_off);
+  a.err = ctx->d_err;
+  cudaError_t e = sws::launch_minimizers(a, sws::SRC_DNA, sws::BAR_READS, tiles, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched minimizer launch");
+  e = sws::launch_pick_offsets_fixup(pick_offsets, nreads, count_out,
+                                     reinterpret_cast<uint64_t *>(ws + L.extra_off), st);
+  if (e != cudaSuccess) return cuda_fail(e, "pick-offset fix-up launch");
+  return SWS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// internal.h -- declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sws {
+
+// Tile configurations of the sliding-sum kernels: threads per CTA x elements per thread.
+enum SlideCfg { CFG_SMALL = 0, CFG_LARGE = 1, CFG_COUNT = 2 };
+
+struct SlideLaunch {
+  int op;       // SWS_OP_*
+  int variant;  // SWS_VARIANT_BLOCK_COMBINE / DOUBLING / PREFIX_DIFF
+  int cfg;      // SlideCfg
+};
+
+// Tile length (elements) of a configuration for elements of `esize` bytes.
+int slide_tile_len(int cfg, int esize);
+// Outputs per tile, or 0 when w does not fit the configuration.
+int slide_tile_outputs(int cfg, int esize, int w);
+
+// Queue one sliding sum; the caller has validated the arguments.
+cudaError_t launch_sliding_sum(const SlideLaunch &L, const void *in, void *out, uint64_t n, int w,
+                               cudaStream_t stream);
+
+// Minimizer kernel parameters (one launch covers one sequence or one read batch).
+struct MiniArgs {
+  const uint8_t *seq;    // packed DNA (source DNA)
+  const uint32_t *keys;  // precomputed keys (source KEYS)
+  uint64_t n;            // bases or keys
+  int k, w, mode;
+  const int64_t *bar;    // N-block pairs, or read offsets (nreads + 1) in batch mode
+  uint64_t nbar;         // number of N-blocks, or number of reads
+  void *hash_out;
+  uint32_t *pos_out;
+  uint64_t capacity;
+  uint64_t *count_out;
+  uint64_t *pick_offsets;  // batch mode: [nreads + 1]
+  // workspace
+  unsigned long long *status;  // one word per tile, zeroed before the launch
+  unsigned int *tile_counter;  // zeroed before the launch
+  uint2 *tile_bar;             // one word per tile (filled by the launcher when barriers exist)
+  int *err;                    // device error word of the context
+};
+
+enum MiniSource { SRC_DNA = 0, SRC_KEYS = 1 };
+enum MiniBarrier { BAR_NBLOCK = 0, BAR_READS = 1 };
+
+// Windows per tile for a given w (a multiple of 64), 0 if w is too large.
+int mini_tile_windows(int w);
+// Number of tiles of a launch over `nwin` window positions (nwin may be 0).
+uint64_t mini_num_tiles(uint64_t nwin, int w);
+// Queue the minimizer kernel; workspace words must already be zeroed on `stream`.
+cudaError_t launch_minimizers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, cudaStream_t stream);
+// Batch fix-up: reads without picks get the offset of the next read that has some.
+cudaError_t launch_pick_offsets_fixup(uint64_t *pick_offsets, uint64_t nreads, const uint64_t *count,
+                                      uint64_t *scratch, cudaStream_t stream);
+// k-mer values.
+cudaError_t launch_kmers(const uint8_t *seq, uint64_t n, int k, int kind, void *out, int *err, cudaStream_t stream);
+
+// Device error bits.
+enum DevErr { DEVERR_LOOKBACK_TIMEOUT = 1, DEVERR_COPY_TIMEOUT = 2 };
+
+}  // namespace sws

@@ -1,0 +1,713 @@
+// minimizer.cu -- k-mers, canonical hashed k-mers and (w,k)-minimizers (Sec. 2.4), fused into
+// one pass per CTA tile.
+//
+// A k-mer is the sliding sum of k bases under concatenation (Sec. 2.4).  With the packed layout
+// (base i at bits 2i.. of the little-endian bit stream) a 32- or 64-bit funnel shift at bit 2i
+// yields bases i, i+1, ... in ascending bit pairs, which is already the reverse complement after
+// a bitwise NOT; the forward k-mer is the same word with its 2-bit groups reversed.  So each
+// k-mer costs O(1) no matter what k is -- the "recurrent" form of a sliding sum (Sec. 5).
+//
+// Minimizers: for each window p the least key among k-mers p .. p+w-1, keys ordered by (value,
+// position), is the sliding minimum of Eq. 2 with (+) = min; it is computed with the
+// block-combine routine (common.cuh), O(1) per window.  Consecutive windows with the same pick
+// store it once (Sec. 2.4, Fig. 2).  Output order is the order of positions, so tiles place
+// their picks with a decoupled look-back over per-tile counts: a tile takes its index from an
+// atomic counter (so every predecessor is already running), publishes its count, and sums its
+// predecessors' counts, waiting at most a bounded time.
+#include <cstdio>
+#include <type_traits>
+
+#include "../../include/sws.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace sws {
+
+namespace {
+
+constexpr int MNT = 256;  // threads per CTA
+constexpr int MVPT = 16;  // k-mers per thread
+constexpr int ML = MNT * MVPT;
+constexpr int MAXB = 128;                 // barriers kept in shared memory per tile
+constexpr int STAGE_BYTES_MINI = ((MNT + 6) * 4 + 15) / 16 * 16;
+constexpr int STAGE_BYTES_KMER = ((MNT + 3) * 4 + 15) / 16 * 16;
+constexpr unsigned long long FLAG_AGG = 1ull << 62;
+constexpr unsigned long long FLAG_INC = 2ull << 62;
+constexpr unsigned long long FLAG_ERR = 3ull << 62;
+constexpr unsigned long long VALUE_MASK = (1ull << 62) - 1;
+constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;  // x >= 64 ns sleep: about a second at most
+constexpr int COPY_SPIN_LIMIT = 1 << 22;
+
+// ---- PTX helpers ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One-dimensional TMA copy global -> shared (16-byte aligned addresses, size multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  return v;
+}
+
+// Stage bytes [gb0, gb0 + sbytes) of the packed sequence into shared memory (zeros outside
+// [0, nbytes)).  The 16-byte-aligned interior goes by one TMA bulk copy completed on an
+// mbarrier; the ragged edge bytes are loaded by the threads.  Returns false (and records the
+// fault) if the copy did not complete within the spin limit.
+__device__ bool stage_bytes(uint8_t *sdst, const uint8_t *__restrict__ seq, uint64_t nbytes, long long gb0,
+                            int sbytes, unsigned long long *bar, int *err) {
+  const long long lo = gb0 > 0 ? gb0 : 0;
+  long long hi = gb0 + sbytes;
+  if (hi > (long long)nbytes) hi = (long long)nbytes;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(seq) & 15u) == 0);
+  const long long bulk = (aligned && hi > lo) ? ((hi - lo) & ~15ll) : 0;
+  if (threadIdx.x == 0 && bulk > 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, (uint32_t)bulk);
+    bulk_g2s(sdst + (lo - gb0), seq + lo, (uint32_t)bulk, bar);
+  }
+  for (int b = threadIdx.x; b < sbytes; b += blockDim.x) {
+    const long long g = gb0 + b;
+    if (g >= lo && g < lo + bulk) continue;
+    sdst[b] = (g >= 0 && g < (long long)nbytes) ? seq[g] : (uint8_t)0;
+  }
+  __syncthreads();
+  bool ok = true;
+  if (bulk > 0) {
+    int spins = 0;
+    while (!mbar_try_wait(bar, 0)) {
+      if (++spins > COPY_SPIN_LIMIT) {
+        ok = false;
+        break;
+      }
+      __nanosleep(32);
+    }
+    if (!ok) {
+      atomicOr(err, DEVERR_COPY_TIMEOUT);
+      // give the copy one more bounded chance to land before the CTA can exit
+      for (int s = 0; s < COPY_SPIN_LIMIT && !mbar_try_wait(bar, 0); ++s) __nanosleep(64);
+    }
+  }
+  return ok;
+}
+
+// ---- k-mer arithmetic -----------------------------------------------------------------------
+// Wang's 64-bit integer mix, written in its multiplicative form, truncated to the mask m after
+// every step (a bijection on [0, m]).
+__device__ __forceinline__ uint32_t wang_mix32(uint32_t x, uint32_t m) {
+  x = (x * 0x1FFFFFu + 0xFFFFFFFFu) & m;  // (x << 21) - x - 1
+  x ^= x >> 24;
+  x = (x * 265u) & m;
+  x ^= x >> 14;
+  x = (x * 21u) & m;
+  x ^= x >> 28;
+  x = (x * 0x80000001u) & m;
+  return x;
+}
+__device__ __forceinline__ unsigned long long wang_mix64(unsigned long long x, unsigned long long m) {
+  x = (x * 0x1FFFFFull + 0xFFFFFFFFFFFFFFFFull) & m;
+  x ^= x >> 24;
+  x = (x * 265ull) & m;
+  x ^= x >> 14;
+  x = (x * 21ull) & m;
+  x ^= x >> 28;
+  x = (x * 0x80000001ull) & m;
+  return x;
+}
+// Reverse the order of the 2-bit groups of a word.
+__device__ __forceinline__ uint32_t rev_pairs32(uint32_t x) {
+  x = __brev(x);
+  return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+__device__ __forceinline__ unsigned long long rev_pairs64(unsigned long long x) {
+  x = __brevll(x);
+  return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+// (fwd, rc, canonical, hash, key-value) of one k-mer from the bases in the low bits of x.
+struct Kmer32 {
+  uint32_t fwd, rc;
+};
+__device__ __forceinline__ Kmer32 kmer32(uint32_t x, int k, uint32_t kmask) {
+  Kmer32 r;
+  r.rc = ~x & kmask;
+  r.fwd = rev_pairs32(x) >> (32 - 2 * k);
+  return r;
+}
+struct Kmer64 {
+  unsigned long long fwd, rc;
+};
+__device__ __forceinline__ Kmer64 kmer64(unsigned long long x, int k, unsigned long long kmask) {
+  Kmer64 r;
+  r.rc = ~x & kmask;
+  r.fwd = rev_pairs64(x) >> (64 - 2 * k);
+  return r;
+}
+__device__ __forceinline__ uint32_t key_value32(const Kmer32 &q, int mode, uint32_t kmask) {
+  if (mode == SWS_MINI_FWD) return q.fwd;
+  const uint32_t c = q.fwd < q.rc ? q.fwd : q.rc;
+  return mode == SWS_MINI_CANONICAL ? c : wang_mix32(c, kmask);
+}
+__device__ __forceinline__ unsigned long long key_value64(const Kmer64 &q, int mode, unsigned long long kmask) {
+  if (mode == SWS_MINI_FWD) return q.fwd;
+  const unsigned long long c = q.fwd < q.rc ? q.fwd : q.rc;
+  return mode == SWS_MINI_CANONICAL ? c : wang_mix64(c, kmask);
+}
+
+// ---- keys -----------------------------------------------------------------------------------
+template <class KOp>
+struct KeyTraits;
+template <>
+struct KeyTraits<OpMinKey64> {
+  using T = unsigned long long;
+  static __device__ __forceinline__ T make(unsigned long long h, uint32_t pos) { return (h << 32) | pos; }
+  static __device__ __forceinline__ uint32_t pos(T k) { return (uint32_t)k; }
+  static __device__ __forceinline__ unsigned long long hash(T k) { return k >> 32; }
+  static __device__ __forceinline__ T none() { return ~0ull; }
+};
+template <>
+struct KeyTraits<OpMinKey96> {
+  using T = Key96;
+  static __device__ __forceinline__ T make(unsigned long long h, uint32_t pos) {
+    return Key96{(uint32_t)h, (uint32_t)(h >> 32), pos};
+  }
+  static __device__ __forceinline__ uint32_t pos(T k) { return k.pos; }
+  static __device__ __forceinline__ unsigned long long hash(T k) { return OpMinKey96::h(k); }
+  static __device__ __forceinline__ T none() { return OpMinKey96::identity(); }
+};
+
+// Look-back over the per-tile status words (warp 0 of a CTA).  Returns the number of picks of
+// all earlier tiles; sets `failed` if a wait ran out or an earlier tile failed.
+__device__ unsigned long long lookback(unsigned long long *status, uint32_t tile, unsigned long long agg, int *err,
+                                       bool &failed) {
+  const int lane = threadIdx.x & 31;
+  failed = false;
+  if (tile == 0) {
+    if (lane == 0) st_relaxed(&status[0], FLAG_INC | agg);
+    return 0;
+  }
+  if (lane == 0) st_relaxed(&status[tile], FLAG_AGG | agg);
+  unsigned long long excl = 0;
+  long long base = (long long)tile - 1;
+  while (true) {
+    const long long idx = base - lane;
+    unsigned long long s = FLAG_INC;
+    int spins = 0;
+    while (true) {
+      s = idx >= 0 ? ld_relaxed(&status[idx]) : FLAG_INC;
+      if (__all_sync(kFull, (s >> 62) != 0ull)) break;
+      if (++spins > LOOKBACK_SPIN_LIMIT) {
+        failed = true;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (failed) break;
+    if (__ballot_sync(kFull, (s >> 62) == 3ull)) {
+      failed = true;
+      break;
+    }
+    const unsigned inc = __ballot_sync(kFull, (s >> 62) == 2ull);
+    unsigned long long v = s & VALUE_MASK;
+    if (inc) {
+      const int first = __ffs(inc) - 1;
+      if (lane > first) v = 0;
+      excl += warp_sum_u64(v);
+      break;
+    }
+    excl += warp_sum_u64(v);
+    base -= 32;
+  }
+  if (lane == 0) {
+    if (failed) {
+      st_relaxed(&status[tile], FLAG_ERR);
+      atomicOr(err, DEVERR_LOOKBACK_TIMEOUT);
+    } else {
+      st_relaxed(&status[tile], FLAG_INC | (excl + agg));
+    }
+  }
+  return excl;
+}
+
+// ---- the fused minimizer kernel --------------------------------------------------------------
+template <class KOp, int SRC, int BAR>
+struct MiniSmem {
+  using BC = BlockCombine<KOp, MNT, MVPT>;
+  static constexpr int OFF_BASES = 0;
+  static constexpr int OFF_BC = STAGE_BYTES_MINI;
+  static constexpr int OFF_BAR = OFF_BC + ((int)sizeof(typename BC::Shared) + 15) / 16 * 16;
+  static constexpr int BYTES = OFF_BAR + MAXB * 16;
+};
+
+template <class KOp, int SRC, int BAR>
+__global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span, uint64_t nwin,
+                                                    const uint2 *__restrict__ tile_bar) {
+  using BC = BlockCombine<KOp, MNT, MVPT>;
+  using KT = KeyTraits<KOp>;
+  using Key = typename KT::T;
+  using SM = MiniSmem<KOp, SRC, BAR>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint8_t *sbases = smem + SM::OFF_BASES;
+  typename BC::Shared &sbc = *reinterpret_cast<typename BC::Shared *>(smem + SM::OFF_BC);
+  long long *sbar = reinterpret_cast<long long *>(smem + SM::OFF_BAR);
+  __shared__ unsigned long long s_mbar;
+  __shared__ uint32_t s_tile;
+  __shared__ int s_phase;
+  __shared__ uint32_t s_last_pos[MNT];
+  __shared__ unsigned char s_last_valid[MNT];
+  __shared__ uint32_t s_wcount[MNT / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ int s_failed;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const long long p0 = (long long)tile * TW;  // first emitted window of the tile
+  const long long ifirst = p0 - 1;             // k-mer / window of local index 0
+
+  // Barriers (N-blocks or read starts) that can touch this tile's windows.
+  uint32_t g_lo = 0, nb = 0;
+  if (tile_bar != nullptr) {
+    const uint2 tb = tile_bar[tile];
+    g_lo = tb.x;
+    nb = tb.y;
+  }
+  const bool bar_in_smem = nb <= (uint32_t)MAXB;
+  if (bar_in_smem) {
+    for (uint32_t i = t; i < nb; i += MNT) {
+      if (BAR == BAR_NBLOCK) {
+        sbar[2 * i] = a.bar[2 * (g_lo + i)];
+        sbar[2 * i + 1] = a.bar[2 * (g_lo + i) + 1];
+      } else {
+        const long long s = a.bar[g_lo + i + 1];
+        sbar[2 * i] = s;
+        sbar[2 * i + 1] = s;
+      }
+    }
+  }
+  auto bar_start = [&](uint32_t i) -> long long {
+    if (bar_in_smem) return sbar[2 * i];
+    return BAR == BAR_NBLOCK ? a.bar[2 * (g_lo + i)] : a.bar[g_lo + i + 1];
+  };
+  auto bar_end = [&](uint32_t i) -> long long {
+    if (bar_in_smem) return sbar[2 * i + 1];
+    return BAR == BAR_NBLOCK ? a.bar[2 * (g_lo + i) + 1] : a.bar[g_lo + i + 1];
+  };
+
+  // Keys of this thread's MVPT k-mers.
+  Key x[MVPT];
+  bool ok = true;
+  if (SRC == SRC_DNA) {
+    if (t == 0) s_phase = (int)((unsigned long long)(ifirst + a.w) % (unsigned long long)a.w);
+    ok = stage_bytes(sbases, a.seq, (a.n + 3) / 4, p0 / 4 - 16, STAGE_BYTES_MINI, &s_mbar, a.err);
+    const uint32_t *W = reinterpret_cast<const uint32_t *>(sbases);
+    const int k = a.k;
+    if (2 * k <= 32) {
+      const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+      const uint32_t w0 = W[3 + t], w1 = W[4 + t], w2 = W[5 + t];
+#pragma unroll
+      for (int j = 0; j < MVPT; ++j) {
+        // k-mer j of this thread starts at bit 126 + 32 t + 2 j of the staged bytes
+        const uint32_t bits = j == 0 ? __funnelshift_r(w0, w1, 30) : __funnelshift_r(w1, w2, 2 * (j - 1));
+        const long long i = ifirst + t * MVPT + j;
+        const Kmer32 q = kmer32(bits, k, kmask);
+        const uint32_t v = key_value32(q, a.mode, kmask);
+        x[j] = (i >= 0 && (unsigned long long)i + k <= a.n) ? KT::make(v, (uint32_t)i) : KT::none();
+      }
+    } else {
+      const unsigned long long kmask = 0xFFFFFFFFFFFFFFFFull >> (64 - 2 * k);
+      const uint32_t w0 = W[3 + t], w1 = W[4 + t], w2 = W[5 + t], w3 = W[6 + t];
+#pragma unroll
+      for (int j = 0; j < MVPT; ++j) {
+        uint32_t lo32, hi32;
+        if (j == 0) {
+          lo32 = __funnelshift_r(w0, w1, 30);
+          hi32 = __funnelshift_r(w1, w2, 30);
+        } else {
+          lo32 = __funnelshift_r(w1, w2, 2 * (j - 1));
+          hi32 = __funnelshift_r(w2, w3, 2 * (j - 1));
+        }
+        const unsigned long long bits = ((unsigned long long)hi32 << 32) | lo32;
+        const long long i = ifirst + t * MVPT + j;
+        const Kmer64 q = kmer64(bits, k, kmask);
+        const unsigned long long v = key_value64(q, a.mode, kmask);
+        x[j] = (i >= 0 && (unsigned long long)i + k <= a.n) ? KT::make(v, (uint32_t)i) : KT::none();
+      }
+    }
+  } else {
+    if (t == 0) s_phase = (int)((unsigned long long)(ifirst + a.w) % (unsigned long long)a.w);
+#pragma unroll
+    for (int j = 0; j < MVPT; ++j) {
+      const long long i = ifirst + t * MVPT + j;
+      x[j] = (i >= 0 && (unsigned long long)i < a.n) ? KT::make(__ldg(a.keys + i), (uint32_t)i) : KT::none();
+    }
+    __syncthreads();
+  }
+
+  // Sliding minimum over w keys (block-combine).
+  const int r0 = (int)(((unsigned)s_phase + (unsigned)(t * MVPT)) % (unsigned)a.w);
+  Key m[MVPT];
+  BC::run(sbc, x, r0, a.w, m);
+
+  // Window validity: inside [0, nwin) and touching no barrier.
+  const long long pf = ifirst + t * MVPT;  // this thread's first window
+  unsigned vmask = 0;
+  uint32_t q = 0;
+  {
+    // first barrier with end > pf (binary search over the tile's list)
+    uint32_t lo = 0, hi = nb;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (bar_end(mid) > pf) hi = mid;
+      else lo = mid + 1;
+    }
+    q = lo;
+  }
+  uint32_t read_of_first = 0;
+  if (BAR == BAR_READS) read_of_first = g_lo + q;
+  uint32_t qj[MVPT];
+#pragma unroll
+  for (int j = 0; j < MVPT; ++j) {
+    const long long p = pf + j;
+    while (q < nb && bar_end(q) <= p) ++q;
+    qj[j] = q;
+    const bool in_range = p >= 0 && (unsigned long long)p < nwin;
+    const bool clear = (q == nb) || (bar_start(q) > p + span - 1);
+    vmask |= (unsigned)(in_range && clear && ok) << j;
+  }
+  (void)read_of_first;
+
+  // Deduplicate: window o emits iff valid and (previous invalid or a different pick).
+  s_last_pos[t] = KT::pos(m[MVPT - 1]);
+  s_last_valid[t] = (unsigned char)((vmask >> (MVPT - 1)) & 1u);
+  __syncthreads();
+  uint32_t prev_pos = t > 0 ? s_last_pos[t - 1] : 0u;
+  bool prev_valid = t > 0 ? (s_last_valid[t - 1] != 0) : false;
+  unsigned emask = 0, firstmask = 0;
+#pragma unroll
+  for (int j = 0; j < MVPT; ++j) {
+    const int o = t * MVPT + j;
+    const bool v = (vmask >> j) & 1u;
+    const uint32_t pp = KT::pos(m[j]);
+    const bool e = v && o >= 1 && o <= TW && (!prev_valid || pp != prev_pos);
+    emask |= (unsigned)e << j;
+    firstmask |= (unsigned)(e && !prev_valid) << j;
+    prev_pos = pp;
+    prev_valid = v;
+  }
+
+  // CTA exclusive scan of pick counts.
+  const uint32_t cnt = __popc(emask);
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, inc, d);
+    if (lane >= d) inc += u;
+  }
+  if (lane == 31) s_wcount[warp] = inc;
+  __syncthreads();
+  uint32_t woff = 0, total = 0;
+#pragma unroll
+  for (int i = 0; i < MNT / 32; ++i) {
+    const uint32_t c = s_wcount[i];
+    if (i < warp) woff += c;
+    total += c;
+  }
+  const uint32_t toff = woff + inc - cnt;  // picks of this tile before this thread
+
+  if (warp == 0) {
+    bool failed = false;
+    const unsigned long long ex = lookback(a.status, tile, total, a.err, failed);
+    if (lane == 0) {
+      s_excl = ex;
+      s_failed = failed ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (s_failed) return;
+  const unsigned long long base = s_excl;
+
+  // Stage picks in shared memory (reusing the block-combine buffer), then store coalesced.
+  using HashT = typename std::conditional<sizeof(Key) == 8, uint32_t, unsigned long long>::type;
+  HashT *sh_hash = reinterpret_cast<HashT *>(&sbc);
+  uint32_t *sh_pos = reinterpret_cast<uint32_t *>(sh_hash + ML);
+  uint32_t r = toff;
+#pragma unroll
+  for (int j = 0; j < MVPT; ++j) {
+    if ((emask >> j) & 1u) {
+      const long long p = pf + j;
+      uint32_t pos = KT::pos(m[j]);
+      if (BAR == BAR_READS) {
+        const uint32_t rd = g_lo + qj[j];  // read index of window p
+        pos = (uint32_t)((long long)pos - a.bar[rd]);
+        if ((firstmask >> j) & 1u) a.pick_offsets[rd] = base + r;
+      }
+      (void)p;
+      sh_hash[r] = (HashT)KT::hash(m[j]);
+      sh_pos[r] = pos;
+      ++r;
+    }
+  }
+  __syncthreads();
+  HashT *gh = static_cast<HashT *>(a.hash_out);
+  for (uint32_t i = t; i < total; i += MNT) {
+    const unsigned long long gi = base + i;
+    if (gi < a.capacity) {
+      gh[gi] = sh_hash[i];
+      a.pos_out[gi] = sh_pos[i];
+    }
+  }
+  if (t == 0 && (unsigned long long)tile * TW + TW >= nwin) {
+    // the tile holding the last window knows the final count
+    *a.count_out = base + total;
+  }
+}
+
+// Per tile: the first barrier that can touch its windows and how many can.
+template <int BAR>
+__global__ void k_tile_barriers(const int64_t *__restrict__ bar, uint64_t nbar, uint64_t ntiles, int TW, int span,
+                                uint2 *__restrict__ out) {
+  const uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= ntiles) return;
+  const long long lo_lim = (long long)tile * TW - 1;            // first window of the tile
+  const long long hi_lim = (long long)tile * TW + TW - 1 + span - 1;  // last base any window touches
+  const uint64_t cnt = BAR == BAR_NBLOCK ? nbar : (nbar > 0 ? nbar - 1 : 0);
+  auto start = [&](uint64_t i) -> long long { return BAR == BAR_NBLOCK ? bar[2 * i] : bar[i + 1]; };
+  auto end = [&](uint64_t i) -> long long { return BAR == BAR_NBLOCK ? bar[2 * i + 1] : bar[i + 1]; };
+  uint64_t lo = 0, hi = cnt;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (end(mid) > lo_lim) hi = mid;
+    else lo = mid + 1;
+  }
+  const uint64_t g = lo;
+  lo = g;
+  hi = cnt;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (start(mid) > hi_lim) hi = mid;
+    else lo = mid + 1;
+  }
+  out[tile] = make_uint2((uint32_t)g, (uint32_t)(lo - g));
+}
+
+// ---- k-mer values -----------------------------------------------------------------------------
+template <bool WIDE>
+__global__ void __launch_bounds__(MNT) k_kmers(const uint8_t *__restrict__ seq, uint64_t n, int k, int kind,
+                                               void *__restrict__ out, int *err) {
+  __shared__ __align__(16) uint8_t sb[STAGE_BYTES_KMER];
+  __shared__ unsigned long long s_mbar;
+  const int t = threadIdx.x;
+  const unsigned long long i0 = (unsigned long long)blockIdx.x * ML;
+  stage_bytes(sb, seq, (n + 3) / 4, (long long)(i0 / 4), STAGE_BYTES_KMER, &s_mbar, err);
+  const uint32_t *W = reinterpret_cast<const uint32_t *>(sb);
+  const unsigned long long m = n - (unsigned long long)k + 1;
+  const unsigned long long g = i0 + (unsigned long long)t * MVPT;
+  if (!WIDE) {
+    const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+    const uint32_t w0 = W[t], w1 = W[t + 1];
+    uint32_t v[MVPT];
+#pragma unroll
+    for (int j = 0; j < MVPT; ++j) {
+      const Kmer32 q = kmer32(__funnelshift_r(w0, w1, 2 * j), k, kmask);
+      const uint32_t c = q.fwd < q.rc ? q.fwd : q.rc;
+      v[j] = kind == SWS_KMER_FWD ? q.fwd : kind == SWS_KMER_RC ? q.rc : kind == SWS_KMER_CANONICAL ? c : wang_mix32(c, kmask);
+    }
+    uint32_t *o = static_cast<uint32_t *>(out);
+    if (g + MVPT <= m && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+      store_vec<uint32_t, MVPT>(o + g, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < MVPT; ++j)
+        if (g + j < m) o[g + j] = v[j];
+    }
+  } else {
+    const unsigned long long kmask = 0xFFFFFFFFFFFFFFFFull >> (64 - 2 * k);
+    const uint32_t w0 = W[t], w1 = W[t + 1], w2 = W[t + 2];
+    unsigned long long v[MVPT];
+#pragma unroll
+    for (int j = 0; j < MVPT; ++j) {
+      const uint32_t lo32 = __funnelshift_r(w0, w1, 2 * j), hi32 = __funnelshift_r(w1, w2, 2 * j);
+      const Kmer64 q = kmer64(((unsigned long long)hi32 << 32) | lo32, k, kmask);
+      const unsigned long long c = q.fwd < q.rc ? q.fwd : q.rc;
+      v[j] = kind == SWS_KMER_FWD ? q.fwd : kind == SWS_KMER_RC ? q.rc : kind == SWS_KMER_CANONICAL ? c : wang_mix64(c, kmask);
+    }
+    unsigned long long *o = static_cast<unsigned long long *>(out);
+    if (g + MVPT <= m && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+      store_vec<unsigned long long, MVPT>(o + g, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < MVPT; ++j)
+        if (g + j < m) o[g + j] = v[j];
+    }
+  }
+}
+
+// ---- batch pick offsets: suffix minimum ------------------------------------------------------
+constexpr int FIX_NT = 256, FIX_PER = 4, FIX_BLOCK = FIX_NT * FIX_PER;
+
+__global__ void k_fix_block_min(const uint64_t *__restrict__ po, uint64_t nreads, uint64_t *__restrict__ bmin) {
+  __shared__ uint64_t s[FIX_NT];
+  const uint64_t b0 = (uint64_t)blockIdx.x * FIX_BLOCK;
+  uint64_t v = ~0ull;
+  for (int j = 0; j < FIX_PER; ++j) {
+    const uint64_t i = b0 + (uint64_t)j * FIX_NT + threadIdx.x;
+    if (i < nreads) v = min(v, po[i]);
+  }
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int d = FIX_NT / 2; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) s[threadIdx.x] = min(s[threadIdx.x], s[threadIdx.x + d]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bmin[blockIdx.x] = s[0];
+}
+
+// Exclusive suffix minimum over the block minima, seeded with the total count.
+__global__ void k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks, const uint64_t *__restrict__ count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t carry = *count;
+  for (uint64_t b = nblocks; b-- > 0;) {
+    const uint64_t v = bmin[b];
+    bmin[b] = carry;
+    carry = min(carry, v);
+  }
+}
+
+__global__ void k_fix_apply(uint64_t *__restrict__ po, uint64_t nreads, const uint64_t *__restrict__ bcarry,
+                            const uint64_t *__restrict__ count) {
+  __shared__ uint64_t s[FIX_BLOCK];
+  const uint64_t b0 = (uint64_t)blockIdx.x * FIX_BLOCK;
+  for (int j = threadIdx.x; j < FIX_BLOCK; j += FIX_NT) {
+    const uint64_t i = b0 + j;
+    s[j] = i < nreads ? po[i] : ~0ull;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t carry = bcarry[blockIdx.x];
+    for (int j = FIX_BLOCK - 1; j >= 0; --j) {
+      carry = min(carry, s[j]);
+      s[j] = carry;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < FIX_BLOCK; j += FIX_NT) {
+    const uint64_t i = b0 + j;
+    if (i < nreads) po[i] = s[j];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) po[nreads] = *count;
+}
+
+template <class KOp, int SRC, int BAR>
+cudaError_t launch_mini_t(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, cudaStream_t st) {
+  using SM = MiniSmem<KOp, SRC, BAR>;
+  auto kern = k_minimizers<KOp, SRC, BAR>;
+  const size_t sm = SM::BYTES;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const int TW = mini_tile_windows(a.w);
+  const int span = SRC == SRC_DNA ? a.w + a.k - 1 : a.w;
+  const uint64_t nwin = SRC == SRC_DNA ? (a.n >= (uint64_t)span ? a.n - span + 1 : 0) : (a.n >= (uint64_t)a.w ? a.n - a.w + 1 : 0);
+  kern<<<(unsigned)num_tiles, MNT, sm, st>>>(a, TW, span, nwin, tile_bar);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int mini_tile_windows(int w) {
+  const int tw = (ML - w) / 64 * 64;
+  return tw >= 64 ? tw : 0;
+}
+
+uint64_t mini_num_tiles(uint64_t nwin, int w) {
+  const int tw = mini_tile_windows(w);
+  if (tw == 0 || nwin == 0) return 0;
+  return (nwin + tw - 1) / tw;
+}
+
+cudaError_t launch_minimizers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, cudaStream_t st) {
+  if (num_tiles == 0) return cudaSuccess;
+  if (num_tiles > 0xffffffffull) return cudaErrorInvalidValue;
+  const uint2 *tile_bar = nullptr;
+  const int TW = mini_tile_windows(a.w);
+  const int span = source == SRC_DNA ? a.w + a.k - 1 : a.w;
+  const bool has_bar = source == SRC_DNA && ((barrier == BAR_NBLOCK && a.nbar > 0) || (barrier == BAR_READS && a.nbar > 1));
+  if (has_bar) {
+    uint2 *tb = a.tile_bar;
+    const unsigned blocks = (unsigned)((num_tiles + 255) / 256);
+    if (barrier == BAR_NBLOCK)
+      k_tile_barriers<BAR_NBLOCK><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, tb);
+    else
+      k_tile_barriers<BAR_READS><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, tb);
+    tile_bar = tb;
+  }
+  const bool wide = source == SRC_DNA && 2 * a.k > 32;
+  if (source == SRC_KEYS) return launch_mini_t<OpMinKey64, SRC_KEYS, BAR_NBLOCK>(a, num_tiles, nullptr, st);
+  if (barrier == BAR_READS) {
+    if (wide) return launch_mini_t<OpMinKey96, SRC_DNA, BAR_READS>(a, num_tiles, tile_bar, st);
+    return launch_mini_t<OpMinKey64, SRC_DNA, BAR_READS>(a, num_tiles, tile_bar, st);
+  }
+  if (wide) return launch_mini_t<OpMinKey96, SRC_DNA, BAR_NBLOCK>(a, num_tiles, tile_bar, st);
+  return launch_mini_t<OpMinKey64, SRC_DNA, BAR_NBLOCK>(a, num_tiles, tile_bar, st);
+}
+
+cudaError_t launch_pick_offsets_fixup(uint64_t *po, uint64_t nreads, const uint64_t *count, uint64_t *scratch,
+                                      cudaStream_t st) {
+  const uint64_t nblocks = (nreads + FIX_BLOCK - 1) / FIX_BLOCK;
+  if (nblocks == 0) {
+    k_fix_apply<<<1, FIX_NT, 0, st>>>(po, 0, count, count);
+    return cudaGetLastError();
+  }
+  k_fix_block_min<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch);
+  k_fix_scan<<<1, 32, 0, st>>>(scratch, nblocks, count);
+  k_fix_apply<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kmers(const uint8_t *seq, uint64_t n, int k, int kind, void *out, int *err, cudaStream_t st) {
+  const uint64_t m = n - (uint64_t)k + 1;
+  const uint64_t blocks = (m + ML - 1) / ML;
+  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+  if (2 * k <= 32) k_kmers<false><<<(unsigned)blocks, MNT, 0, st>>>(seq, n, k, kind, out, err);
+  else k_kmers<true><<<(unsigned)blocks, MNT, 0, st>>>(seq, n, k, kind, out, err);
+  return cudaGetLastError();
+}
+
+}  // namespace sws

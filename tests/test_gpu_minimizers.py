@@ -1,0 +1,129 @@
+"""GPU k-mers and minimizers (Sec. 2.4) against the oracle, bit for bit, through the C ABI."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_10074_gb300 import binding as B
+from paper_1811_10074_gb300 import synth
+from gpu_common import random_nblocks, require_gpu, to_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+# ---------------------------------------------------------------------------------------------
+# k-mers
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 5, 15, 16, 17, 19, 31, 32])
+@pytest.mark.parametrize("n", [1, 16, 17, 4095, 4096 + 40, 100_003])
+def test_kmers_match_oracle(k, n):
+    seq = synth.acgt_uniform_packed(n, seed=n + k)
+    sd = seq.cuda()
+    for kind in ("fwd", "rc", "canonical", "hash"):
+        got = B.kmers(sd, n, k, kind)
+        torch.cuda.synchronize()
+        ref = oracle.kmers(seq, n, k, kind)
+        assert got.shape[0] == ref.shape[0]
+        g = to_u64(got)
+        bad = np.nonzero(g != ref)[0]
+        assert bad.size == 0, (kind, bad[:5], g[bad[:5]], ref[bad[:5]])
+
+
+# ---------------------------------------------------------------------------------------------
+# minimizers
+# ---------------------------------------------------------------------------------------------
+
+def check_minimizers(seq_cpu, n, k, w, mode="hash", nblocks=None):
+    nb_t = None if nblocks is None or len(nblocks) == 0 else torch.from_numpy(nblocks).cuda()
+    h, p = B.minimizers(seq_cpu.cuda(), n, k, w, mode, nblocks=nb_t)
+    rh, rp = oracle.minimizers(seq_cpu, n, k, w, mode, nblocks=nblocks)
+    gh, gp = to_u64(h), p.cpu().numpy().view(np.uint32)
+    assert gh.shape == rh.shape, (n, k, w, mode, gh.shape, rh.shape)
+    bad = np.nonzero((gh != rh) | (gp != rp))[0]
+    assert bad.size == 0, (n, k, w, mode, bad[:5], gp[bad[:5]], rp[bad[:5]])
+    return gh, gp
+
+
+def test_minimizers_plain_workload():
+    """1,000,000 uniform i.i.d. bases (seed 42), k=15, w=10, hashed canonical k-mers."""
+    n = 1_000_000
+    seq = synth.acgt_uniform_packed(n, seed=42)
+    gh, gp = check_minimizers(seq, n, 15, 10)
+    dens = gh.size / (n - 14)
+    assert abs(dens - 2 / 11) < 0.01
+
+
+@pytest.mark.parametrize("k,w", [(1, 1), (3, 3), (5, 4), (15, 10), (16, 10), (17, 10), (19, 10), (15, 50),
+                                 (31, 2), (32, 7), (11, 257), (15, 1000), (9, 4000)])
+@pytest.mark.parametrize("mode", ["hash", "canonical", "fwd"])
+def test_minimizers_random(k, w, mode):
+    rng = np.random.default_rng(k * 1000 + w)
+    for n in (1, k + w - 2, k + w - 1, k + w, 4032 + k + w, 3 * 4096 + 7, 40_000):
+        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+        check_minimizers(seq, n, k, w, mode)
+
+
+@pytest.mark.parametrize("k,w", [(15, 10), (19, 10), (5, 3), (15, 50)])
+def test_minimizers_with_nblocks(k, w):
+    rng = np.random.default_rng(5 + k + w)
+    for n, count, maxlen in ((5000, 3, 40), (60_000, 30, 3000), (200_000, 400, 50), (30_000, 300, 5)):
+        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+        iv = random_nblocks(n, rng, count, maxlen)
+        check_minimizers(seq, n, k, w, "hash", iv)
+
+
+def test_minimizers_low_complexity_ties():
+    """A repetitive sequence makes many equal keys: the leftmost must win everywhere."""
+    unit = synth.codes_from_string("ACGTTGCAAC")
+    codes = unit.repeat(5000)
+    codes[777] = 3
+    seq = synth.pack_codes(codes)
+    n = codes.numel()
+    for k, w in ((5, 10), (15, 10), (3, 20)):
+        for mode in ("hash", "fwd"):
+            check_minimizers(seq, n, k, w, mode)
+
+
+def test_minimizers_capacity_overflow():
+    n = 50_000
+    seq = synth.acgt_uniform_packed(n, seed=9)
+    rh, rp = oracle.minimizers(seq, n, 15, 10)
+    cap = rh.size // 2
+    h, p, cnt = B.minimizers(seq.cuda(), n, 15, 10, capacity=cap, sync=False)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == rh.size
+    assert (to_u64(h[:cap]) == rh[:cap]).all() and (p[:cap].cpu().numpy().view(np.uint32) == rp[:cap]).all()
+    with pytest.raises(B.SwsError, match="CAPACITY"):
+        B.minimizers(seq.cuda(), n, 15, 10, capacity=cap)
+
+
+def test_minimizers_from_keys():
+    rng = np.random.default_rng(3)
+    for m, w, hi in ((1, 1, 10), (100, 4, 5), (4096 * 3 + 11, 17, 1 << 30), (100_000, 10, 50), (50_000, 1000, 1 << 20)):
+        keys = rng.integers(0, hi, size=m, dtype=np.int64).astype(np.uint32)
+        kd = torch.from_numpy(keys.view(np.int32)).cuda()
+        h, p = B.minimizers_from_keys(kd, w)
+        rh, rp = oracle.minimizers_from_keys(keys.astype(np.uint64), w)
+        assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all(), (m, w)
+
+
+def test_minimizers_batch_matches_per_read_oracle():
+    rng = np.random.default_rng(11)
+    lens = np.concatenate([rng.integers(0, 30, size=50), rng.integers(100, 251, size=400),
+                           rng.integers(1000, 20000, size=12), [0, 0, 5000]])
+    rng.shuffle(lens)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    total = int(offs[-1])
+    seq = synth.acgt_uniform_packed(total, seed=77)
+    for k, w, mode in ((15, 10, "hash"), (19, 10, "hash"), (5, 3, "fwd")):
+        h, p, po = B.minimizers_batch(seq.cuda(), torch.from_numpy(offs).cuda(), total, k, w, mode)
+        rh, rp, rpo = oracle.minimizers_batch(seq, offs, k, w, mode)
+        assert (po.cpu().numpy().view(np.uint64) == rpo).all()
+        assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()

@@ -1,0 +1,78 @@
+"""GPU sliding window sum (Eq. 2) against the oracle, element by element, through the C ABI."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_10074_gb300 import binding as B
+from gpu_common import assert_sliding_equal, make_input, oracle_sliding, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["add_i32", "min_i32", "max_i32", "xor_i32", "affine_u32", "add_f32"]
+INT_OPS = ["add_i32", "min_i32", "max_i32", "xor_i32"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def variants_for(op):
+    v = ["block_combine", "doubling", "auto"]
+    if op in ("add_i32", "xor_i32"):
+        v.append("prefix_diff")
+    return v
+
+
+# (w, n) pairs: empty, exact, one tile, tile edges, several tiles with a ragged tail
+CASES = [(1, 1), (1, 4097), (2, 1), (2, 2), (3, 10), (4, 4095), (4, 4096 + 3), (7, 9000), (16, 16), (16, 24593),
+         (33, 40000), (64, 100_003), (255, 30000), (256, 70_001), (1024, 1023), (1024, 1024), (1024, 50_000),
+         (1025, 33333), (2048, 30000)]
+
+
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("w,n", CASES)
+def test_sliding_sum_matches_oracle(op, w, n):
+    x, ref = oracle_sliding(op, w, n, 7, op in INT_OPS)
+    xd = x.cuda()
+    for variant in variants_for(op):
+        if variant == "doubling" and w > 1100 and op == "affine_u32":
+            continue  # covered at smaller w; keeps the suite short
+        y = B.sliding_sum(op, w, xd, variant=variant)
+        torch.cuda.synchronize()
+        assert y.shape[0] == max(n - w + 1, 0)
+        if y.shape[0]:
+            assert_sliding_equal(op, w, x, y, ref)
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_unaligned_pointers(op):
+    """Views that start one element into a buffer disable the 16-byte vector path."""
+    n, w = 20011, 37
+    x, _ = oracle_sliding(op, w, n + 1, 3, False)
+    xd = x.cuda()[1:]
+    ref = oracle.sliding_sum(op, w, x[1:])
+    buf = torch.empty((n - w + 2,) + tuple(x.shape[1:]), dtype=x.dtype, device="cuda")
+    y = B.sliding_sum(op, w, xd, out=buf[1:])
+    torch.cuda.synchronize()
+    assert_sliding_equal(op, w, x[1:], y, ref)
+
+
+def test_n_smaller_than_w_writes_nothing():
+    x = make_input("add_i32", 10).cuda()
+    out = torch.full((4,), 12345, dtype=torch.int32, device="cuda")
+    y = B.sliding_sum("add_i32", 11, x, out=out[:0])
+    torch.cuda.synchronize()
+    assert y.numel() == 0 and (out == 12345).all()
+
+
+def test_invalid_arguments_are_rejected():
+    x = make_input("add_i32", 100).cuda()
+    with pytest.raises(B.SwsError, match="INVALID"):
+        B.sliding_sum("add_i32", 0, x)
+    with pytest.raises(B.SwsError, match="INVALID"):
+        B.sliding_sum("min_i32", 4, x, variant="prefix_diff")
+    with pytest.raises(B.SwsError, match="INVALID"):
+        B.sliding_sum("add_i32", 4, x, out=x[:97])  # overlapping
