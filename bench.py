@@ -47,8 +47,18 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1 << 28, help="elements per sliding-sum input")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
+    ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
+    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers"],
+                    help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
-    return ap.parse_args()
+    ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
+    args = ap.parse_args()
+    args.ops = [o for o in args.ops.split(",") if o]
+    args.ws = [int(v) for v in args.ws.split(",") if v]
+    return args
 
 
 # ------------------------------------------------------------------------------------------
@@ -190,7 +200,7 @@ def run_ours(args, world, rank, local):
         outs[op] = torch.empty((n,) + tuple(x.shape[1:]), dtype=x.dtype, device=dev)
     ctx = P.default_context(dev.index)
     stream = torch.cuda.current_stream()
-    cases = [(op, w) for op in OPS for w in WS]
+    cases = [(op, w) for op in args.ops for w in args.ws]
     step_bytes = sum(case_bytes(op, w, n) for op, w in cases)
 
     def step(events=None):
@@ -238,38 +248,9 @@ def run_ours(args, world, rank, local):
     achieved = tot_b / (tot_ms / 1e3) / 1e9
 
     # end to end through the public API with pinned host buffers
-    hx = {op: xs[op].cpu().pin_memory() for op in ("add_i32", "affine_u32", "add_f32")}
-    hx.update({"min_i32": hx["add_i32"], "max_i32": hx["add_i32"], "xor_i32": hx["add_i32"]})
-    hy = {op: torch.empty(outs[op].shape, dtype=outs[op].dtype).pin_memory() for op in OPS}
-    h2d = d2h = 0
-
-    def e2e_step():
-        nonlocal h2d, d2h
-        h2d = d2h = 0
-        for op in OPS:
-            xs[op].copy_(hx[op], non_blocking=True)
-            h2d += hx[op].numel() * hx[op].element_size()
-            for w in WS:
-                m = n - w + 1
-                P.sliding_sum(op, w, xs[op], out=outs[op][:m], ctx=ctx, stream=stream)
-                hy[op][:m].copy_(outs[op][:m], non_blocking=True)
-                d2h += hy[op][:m].numel() * hy[op].element_size()
-
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
-    e_start.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e_ms = max_over_ranks(world, e_start.elapsed_time(e_end)) / args.steps
-    e2e_value = world * step_bytes / (e_ms / 1e3) / 1e9
-    del hx, hy
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg(args, world, xs, outs, ctx, stream, step_bytes)
 
     result = {
         "metric": METRIC,
@@ -291,21 +272,62 @@ def run_ours(args, world, rank, local):
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                      "traffic": None, "per_case_gbs": per_case},
-        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(e_ms, 3)},
+        "e2e": e2e,
         "gpu_launches": len(cases) * args.steps,
         "clocks": clk,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         v, dt = cpu_baseline(args.cpu_sample)
         result["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                   "sample": f"{args.cpu_sample} elements per (op, w) case, all 30 cases, "
                                             f"{dt:.1f} s single-threaded naive O(wN)"}
     if not args.no_extras and rank == 0:
-        result["minimizers"] = minimizer_extras(dev, ctx)
+        result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
     del xs, outs
     torch.cuda.empty_cache()
     return result
+
+
+def e2e_leg(args, world, xs, outs, ctx, stream, step_bytes):
+    """The same sweep through the public API from pinned host buffers: every step copies each
+    operator's input to the device, runs its sliding sums and copies every output back."""
+    import paper_1811_10074_gb300 as P
+    n = args.n
+    ops = list(dict.fromkeys(args.ops))
+    hx = {}
+    for op in ops:
+        src = "add_i32" if op in ("min_i32", "max_i32", "xor_i32") else op
+        if src not in hx:
+            hx[src] = xs[src].cpu().pin_memory()
+        hx[op] = hx[src]
+    hy = {op: torch.empty(outs[op].shape, dtype=outs[op].dtype).pin_memory() for op in ops}
+    nbytes = {"h2d": 0, "d2h": 0}
+
+    def e2e_step():
+        nbytes["h2d"] = nbytes["d2h"] = 0
+        for op in ops:
+            xs[op].copy_(hx[op], non_blocking=True)
+            nbytes["h2d"] += hx[op].numel() * hx[op].element_size()
+            for w in args.ws:
+                m = n - w + 1
+                P.sliding_sum(op, w, xs[op], out=outs[op][:m], ctx=ctx, stream=stream)
+                hy[op][:m].copy_(outs[op][:m], non_blocking=True)
+                nbytes["d2h"] += hy[op][:m].numel() * hy[op].element_size()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e_ms = max_over_ranks(world, e_start.elapsed_time(e_end)) / args.steps
+    return {"value": round(world * step_bytes / (e_ms / 1e3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": nbytes["h2d"], "d2h_bytes_per_step": nbytes["d2h"], "ms_per_step": round(e_ms, 3)}
 
 
 def time_call(fn, reps: int, stream):
@@ -321,7 +343,7 @@ def time_call(fn, reps: int, stream):
     return a.elapsed_time(b) / reps
 
 
-def minimizer_extras(dev, ctx):
+def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
     """Secondary numbers: fused minimizers (Gbp/s) and the paper-equivalent sliding minimum over
     precomputed hashes (GB/s vs HBM)."""
     import paper_1811_10074_gb300 as P
@@ -336,8 +358,9 @@ def minimizer_extras(dev, ctx):
     ms = time_call(lambda: P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False), 50, stream)
     out["plain_1e6"] = {"ms_per_call": round(ms, 4), "gbp_s": round(n / (ms / 1e3) / 1e9, 2),
                         "picks": int(cnt.item()), "k": 15, "w": 10}
-    # long sequence: 2^31 uniform bases (k=15 w=10 and k=19 w=10)
-    n = 1 << 31
+    # long sequence: uniform bases (default 2^31), k=15 w=10, k=19 w=10, k=15 w=50
+    n = long_n
+    tag = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
     seq = synth.acgt_uniform_packed(n, seed=43, device=dev)
     for k, w in ((15, 10), (19, 10), (15, 50)):
         cap = int(n * 2.6 / (w + 1)) + 1024
@@ -346,7 +369,7 @@ def minimizer_extras(dev, ctx):
         picks = int(cnt.item())
         hb = 4 if 2 * k <= 32 else 8
         bytes_ = n / 4 + picks * (hb + 4)
-        out[f"fused_2^31_k{k}_w{w}"] = {"ms": round(ms, 3), "gbp_s": round(n / (ms / 1e3) / 1e9, 1),
+        out[f"fused_{tag}_k{k}_w{w}"] = {"ms": round(ms, 3), "gbp_s": round(n / (ms / 1e3) / 1e9, 1),
                                         "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
     del seq
     torch.cuda.empty_cache()
@@ -405,6 +428,14 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    if args.section == "minimizers":
+        from paper_1811_10074_gb300 import build as B
+        import paper_1811_10074_gb300 as P
+        B.build()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if rank == 0:
+            print(json.dumps({"minimizers": minimizer_extras(dev, P.default_context(dev.index), args.mini_n)}), flush=True)
         return
     res = run_ours(args, world, rank, local)
     if rank == 0:

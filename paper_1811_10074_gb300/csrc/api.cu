@@ -185,9 +185,9 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   sws::SlideLaunch L;
   L.op = op;
   L.variant = variant == SWS_VARIANT_AUTO ? SWS_VARIANT_BLOCK_COMBINE : variant;
-  // the smaller tile when it keeps the halo re-read under a quarter of the tile
+  // the smaller tile when it keeps the halo re-read under an eighth of the tile
   const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
-  L.cfg = (w - 1) * 4 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
+  L.cfg = (w - 1) * 8 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
   if (sws::slide_tile_outputs(L.cfg, es, w) == 0)
     return fail(SWS_ERR_UNSUPPORTED, "w = %d is larger than the tile of this build", w);
   cudaError_t e = sws::launch_sliding_sum(L, in, out, n, w, static_cast<cudaStream_t>(stream));

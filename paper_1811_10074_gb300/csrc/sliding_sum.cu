@@ -90,6 +90,162 @@ __global__ void __launch_bounds__(NT) k_slide_bc(const typename Op::T *__restric
 }
 
 // ------------------------------------------------------------------------------------------
+// Block-combine, w a multiple of VPT: blocks are whole thread chunks
+// ------------------------------------------------------------------------------------------
+// A tile starts at a multiple of w, so block b of the tile is exactly the G = w / VPT threads
+// bG .. bG+G-1.  In-thread prefix and suffix sums then need no segmentation, the carries are
+// scans over groups of G lanes (lane-aligned when G divides 32; whole warps when G is a
+// multiple of 32), and the shifted read P_{p+w-1} is row t+G of the prefix array, element j-1
+// -- a 16-byte-vector read from a padded row layout that is bank-conflict free.
+template <class Op, int NT, int VPT>
+__global__ void __launch_bounds__(NT) k_slide_al(const typename Op::T *__restrict__ in,
+                                                 typename Op::T *__restrict__ out, uint64_t n, int w, int TO) {
+  using T = typename Op::T;
+  constexpr int NW = NT / 32;
+  constexpr int EPV = 16 / (int)sizeof(T);  // elements per 16-byte unit
+  constexpr int UPR = VPT / EPV;            // 16-byte units per thread row
+  constexpr int ROW = UPR + 1;              // padded row (units)
+  static_assert(VPT % EPV == 0, "rows must be whole 16-byte units");
+  extern __shared__ __align__(16) uint4 sm4[];
+  __shared__ T s_wf[NW], s_wb[NW];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int G = w / VPT;
+  const uint64_t t0 = (uint64_t)blockIdx.x * (uint64_t)TO;
+  const uint64_t g = t0 + (uint64_t)t * VPT;
+  const bool vec = aligned16(in) && aligned16(out);
+  T x[VPT];
+  load_tile<Op, VPT>(in, n, g, vec, x);
+  T P[VPT], S[VPT];
+  P[0] = x[0];
+#pragma unroll
+  for (int j = 1; j < VPT; ++j) P[j] = Op::op(P[j - 1], x[j]);
+  S[VPT - 1] = x[VPT - 1];
+#pragma unroll
+  for (int j = VPT - 2; j >= 0; --j) S[j] = Op::op(x[j], S[j + 1]);
+
+  const int pos = t % G;  // position of this thread inside its block
+  const bool head = pos == 0, tail = pos == G - 1;
+  T cP = P[VPT - 1], cS = S[0];
+  if (G <= 32) {
+    // segments of G lanes, aligned to lane multiples of G
+    const int base = lane - pos;
+    T vf = P[VPT - 1], vb = S[0];
+    for (int d = 1; d < G; d <<= 1) {
+      const T u = shfl_up_t(vf, d);
+      const T v = shfl_down_t(vb, d);
+      if (pos >= d) vf = Op::op(u, vf);
+      if (pos + d < G) vb = Op::op(vb, v);
+    }
+    const T ef = shfl_up_t(vf, 1);
+    const T eb = shfl_down_t(vb, 1);
+    (void)base;
+    cP = ef;
+    cS = eb;
+  } else {
+    // blocks are m = G/32 whole warps: plain warp scans plus carries across the block's warps
+    const int m = G >> 5, wp = warp % m;
+    T vf = warp_seg_scan_fwd<Op>(P[VPT - 1], 0u, lane);
+    T vb = warp_seg_scan_bwd<Op>(S[0], 0u, lane);
+    if (lane == 31) s_wf[warp] = vf;
+    if (lane == 0) s_wb[warp] = vb;
+    __syncthreads();
+    const T ef = shfl_up_t(vf, 1);
+    const T eb = shfl_down_t(vb, 1);
+    T cwf = Op::identity(), cwb = Op::identity();
+    for (int i = warp - wp; i < warp; ++i) cwf = (i == warp - wp) ? s_wf[i] : Op::op(cwf, s_wf[i]);
+    for (int i = warp - wp + m - 1; i > warp; --i) cwb = (i == warp - wp + m - 1) ? s_wb[i] : Op::op(s_wb[i], cwb);
+    if (lane == 0) cP = cwf;
+    else cP = wp > 0 ? Op::op(cwf, ef) : ef;
+    if (lane == 31) cS = cwb;
+    else cS = wp < m - 1 ? Op::op(eb, cwb) : eb;
+  }
+  if (!head) {
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) P[j] = Op::op(cP, P[j]);
+  }
+  if (!tail) {
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) S[j] = Op::op(S[j], cS);
+  }
+  {
+    uint4 u[UPR];
+    memcpy(u, P, sizeof(u));
+#pragma unroll
+    for (int c = 0; c < UPR; ++c) sm4[t * ROW + c] = u[c];
+  }
+  __syncthreads();
+  T y[VPT];
+  int tn = t + G;
+  if (tn > NT - 1) tn = NT - 1;  // only threads whose outputs lie past TO get here
+  {
+    uint4 u[UPR];
+#pragma unroll
+    for (int c = 0; c < UPR; ++c) u[c] = sm4[tn * ROW + c];
+    T Pn[VPT];
+    memcpy(Pn, u, sizeof(u));
+    const T *prow = reinterpret_cast<const T *>(sm4 + (tn - 1) * ROW);
+    const T plast = prow[VPT - 1];
+    y[0] = head ? S[0] : Op::op(S[0], plast);
+#pragma unroll
+    for (int j = 1; j < VPT; ++j) y[j] = Op::op(S[j], Pn[j - 1]);
+  }
+  store_tile<Op, VPT>(out, n - (uint64_t)w + 1, g, t * VPT, TO, vec, y);
+}
+
+// ------------------------------------------------------------------------------------------
+// Block-combine for w in {1, 2, 4, 8} dividing VPT: everything in registers
+// ------------------------------------------------------------------------------------------
+// Each thread owns VPT consecutive outputs starting at a multiple of VPT (hence of W) and loads
+// the VPT + W - 1 inputs they need (the W - 1 extra ones come from the next thread's chunk, out
+// of L1).  Blocks of W are compile-time: S within block b, P within block b+1, one (+) per output.
+template <class Op, int W, int VPT>
+__global__ void __launch_bounds__(256) k_slide_small(const typename Op::T *__restrict__ in,
+                                                     typename Op::T *__restrict__ out, uint64_t n) {
+  using T = typename Op::T;
+  constexpr int EPV = 16 / (int)sizeof(T);
+  constexpr int EXT = W > 1 ? ((W - 1 + EPV - 1) / EPV) * EPV : 0;
+  static_assert(VPT % W == 0, "W must divide VPT");
+  const uint64_t nout = n - (uint64_t)W + 1;
+  const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * (uint64_t)VPT;
+  if (g >= nout) return;
+  const bool vec = aligned16(in) && aligned16(out);
+  T x[VPT + EXT];
+  if (vec && g + VPT + EXT <= n) {
+    T a[VPT];
+    load_vec<T, VPT>(in + g, a);
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) x[j] = a[j];
+    if (EXT > 0) {
+      T b[EXT > 0 ? EXT : EPV];
+      load_vec<T, (EXT > 0 ? EXT : EPV)>(in + g + VPT, b);
+#pragma unroll
+      for (int j = 0; j < EXT; ++j) x[VPT + j] = b[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < VPT + EXT; ++j) x[j] = (g + j < n) ? in[g + j] : Op::identity();
+  }
+  T y[VPT];
+#pragma unroll
+  for (int b = 0; b < VPT / W; ++b) {
+    T S[W], Pn[W > 1 ? W - 1 : 1];
+    S[W - 1] = x[b * W + W - 1];
+#pragma unroll
+    for (int i = W - 2; i >= 0; --i) S[i] = Op::op(x[b * W + i], S[i + 1]);
+    if (W > 1) {
+      Pn[0] = x[(b + 1) * W];
+#pragma unroll
+      for (int i = 1; i < W - 1; ++i) Pn[i] = Op::op(Pn[i - 1], x[(b + 1) * W + i]);
+    }
+    y[b * W] = S[0];
+#pragma unroll
+    for (int i = 1; i < W; ++i) y[b * W + i] = Op::op(S[i], Pn[i - 1]);
+  }
+  store_tile<Op, VPT>(out, nout, g, 0, VPT, vec, y);
+}
+
+// ------------------------------------------------------------------------------------------
 // Doubling
 // ------------------------------------------------------------------------------------------
 template <class Op>
@@ -245,6 +401,15 @@ int tile_outputs(int L, int esize, int w) {
   return to >= align ? to : 0;
 }
 
+// The aligned block-combine applies when blocks are whole thread chunks, blocks of at most a
+// warp divide the warp (or are whole warps), and a tile holds at least one block of outputs.
+bool aligned_blocks_ok(int w, int vpt, int nt, int L) {
+  if (w % vpt != 0) return false;
+  const int G = w / vpt;
+  const bool shape = (G <= 32 && 32 % G == 0) || (G % 32 == 0 && G / 32 <= nt / 32);
+  return shape && (L - w + 1) / w >= 1;
+}
+
 template <class Kern>
 cudaError_t set_smem(Kern kern, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -268,6 +433,26 @@ cudaError_t launch_op(int variant, const void *in, void *out, uint64_t n, int w,
     cudaError_t e = set_smem(kern, sm);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)tiles, S::NT, sm, st>>>(pin, pout, n, w, TO);
+  } else if (w <= 8 && S::VPT % w == 0) {
+    const uint64_t chunks = (nout + S::VPT - 1) / S::VPT;
+    const uint64_t blocks = (chunks + 255) / 256;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    switch (w) {
+      case 1: k_slide_small<Op, 1, S::VPT><<<(unsigned)blocks, 256, 0, st>>>(pin, pout, n); break;
+      case 2: k_slide_small<Op, 2, S::VPT><<<(unsigned)blocks, 256, 0, st>>>(pin, pout, n); break;
+      case 4: k_slide_small<Op, 4, S::VPT><<<(unsigned)blocks, 256, 0, st>>>(pin, pout, n); break;
+      default: k_slide_small<Op, 8, S::VPT><<<(unsigned)blocks, 256, 0, st>>>(pin, pout, n); break;
+    }
+  } else if (aligned_blocks_ok(w, S::VPT, S::NT, S::L)) {
+    const int TOa = (S::L - w + 1) / w * w;
+    const uint64_t tiles_a = (nout + (uint64_t)TOa - 1) / (uint64_t)TOa;
+    if (tiles_a > 0x7fffffffull) return cudaErrorInvalidValue;
+    constexpr int ROW = S::VPT * (int)sizeof(T) / 16 + 1;
+    const size_t sm = (size_t)S::NT * ROW * 16;
+    auto kern = k_slide_al<Op, S::NT, S::VPT>;
+    cudaError_t e = set_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)tiles_a, S::NT, sm, st>>>(pin, pout, n, w, TOa);
   } else {
     const size_t sm = sizeof(typename BlockCombine<Op, S::NT, S::VPT>::Shared);
     auto kern = k_slide_bc<Op, S::NT, S::VPT>;

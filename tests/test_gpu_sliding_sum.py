@@ -27,9 +27,13 @@ def variants_for(op):
 
 
 # (w, n) pairs: empty, exact, one tile, tile edges, several tiles with a ragged tail
-CASES = [(1, 1), (1, 4097), (2, 1), (2, 2), (3, 10), (4, 4095), (4, 4096 + 3), (7, 9000), (16, 16), (16, 24593),
-         (33, 40000), (64, 100_003), (255, 30000), (256, 70_001), (1024, 1023), (1024, 1024), (1024, 50_000),
-         (1025, 33333), (2048, 30000)]
+# Dispatch coverage: w in {1,2,4,8} run fully in registers; multiples of the thread chunk take the
+# aligned block-combine (blocks within a warp, or several whole warps: w = 512, 1024, 1536, 2048);
+# everything else the general segmented block-combine.
+CASES = [(1, 1), (1, 4097), (2, 1), (2, 2), (2, 33), (3, 10), (4, 4095), (4, 4096 + 3), (7, 9000), (8, 8),
+         (8, 50_001), (16, 16), (16, 24593), (32, 20000), (33, 40000), (48, 20000), (64, 100_003), (255, 30000),
+         (256, 70_001), (512, 40000), (1024, 1023), (1024, 1024), (1024, 50_000), (1025, 33333), (1536, 30000),
+         (2048, 30000)]
 
 
 @pytest.mark.parametrize("op", OPS)
