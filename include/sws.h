@@ -139,6 +139,22 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
                                 uint64_t total_bases, int k, int w, int mode, void *hash_out, uint32_t *pos_out,
                                 uint64_t capacity, uint64_t *pick_offsets, uint64_t *count_out, void *stream);
 
+/* ---- seed table (Sec. 2.4, Fig. 1) -------------------------------------------------------- */
+/* Build the seed table from m (hash, position) hits: a position table listing the hits sorted by
+ * hash, and a pointer table with, for every bucket b of hash values (bucket of h =
+ * h >> (hash_bits - bucket_bits)), the index of its first hit.
+ *   hash, pos          : device input; hash is uint32 when hash_bits <= 32, else uint64.  Hits
+ *                        should come in increasing position (as sws_minimizers writes them): the
+ *                        sort is stable, so each hash's hits then stay in position order.
+ *   sorted_hash/pos    : device outputs of m entries (same types); must not overlap the inputs.
+ *   bucket_offsets     : device uint64 [2^bucket_bits + 1]; hits of bucket b are
+ *                        [bucket_offsets[b], bucket_offsets[b+1]); the last entry is m.
+ *   Limits: 1 <= hash_bits <= 64, 0 <= bucket_bits <= min(hash_bits, 32), m < 2^32.
+ * Uses workspace (about 16 bytes per hit, 24 when hash_bits > 32). */
+sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, uint64_t m, int hash_bits,
+                          int bucket_bits, void *sorted_hash, uint32_t *sorted_pos, uint64_t *bucket_offsets,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ SIGNATURES = {
     "sws_minimizers": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
     "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
     "sws_minimizers_batch": (i32, [vp, vp, vp, u64, u64, i32, i32, i32, vp, vp, u64, vp, vp, vp]),
+    "sws_kmer_table": (i32, [vp, vp, vp, u64, i32, i32, vp, vp, vp, vp]),
 }
 
 
@@ -250,3 +251,18 @@ def minimizers_batch(seq: torch.Tensor, offsets: torch.Tensor, total_bases: int,
         return h, p, po, cnt
     h, p, _ = _trim(h, p, cnt, capacity, ctx, stream)
     return h, p, po
+
+
+def kmer_table(hashes: torch.Tensor, pos: torch.Tensor, hash_bits: int, bucket_bits: int,
+               ctx: Context | None = None, stream=None):
+    """Seed table: (sorted hashes, sorted positions, bucket offsets [2^bucket_bits + 1])."""
+    _dev(hashes, "hashes")
+    _dev(pos, "pos")
+    ctx = ctx or default_context(hashes.device.index)
+    m = hashes.shape[0]
+    sh = torch.empty_like(hashes)
+    sp = torch.empty_like(pos)
+    off = torch.empty((1 << bucket_bits) + 1, dtype=torch.int64, device=hashes.device)
+    _check(load().sws_kmer_table(ctx.handle, _ptr(hashes), _ptr(pos), m, int(hash_bits), int(bucket_bits), _ptr(sh),
+                                 _ptr(sp), _ptr(off), _stream(stream)))
+    return sh, sp, off

@@ -323,4 +323,56 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
   return SWS_OK;
 }
 
+sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, uint64_t m, int hash_bits,
+                          int bucket_bits, void *sorted_hash, uint32_t *sorted_pos, uint64_t *bucket_offsets,
+                          void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (hash_bits < 1 || hash_bits > 64) return fail(SWS_ERR_INVALID, "hash_bits must be in [1, 64] (got %d)", hash_bits);
+  if (bucket_bits < 0 || bucket_bits > hash_bits || bucket_bits > 32)
+    return fail(SWS_ERR_INVALID, "bucket_bits must be in [0, min(hash_bits, 32)] (got %d)", bucket_bits);
+  if (m >= (1ull << 32)) return fail(SWS_ERR_INVALID, "at most 2^32 - 1 hits");
+  if (!bucket_offsets) return fail(SWS_ERR_INVALID, "bucket_offsets is NULL");
+  if (m > 0 && (!hash || !pos || !sorted_hash || !sorted_pos)) return fail(SWS_ERR_INVALID, "NULL array");
+  const uint64_t hs = hash_bits > 32 ? 8 : 4;
+  if (m > 0) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(hash), a1 = a0 + m * hs;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(sorted_hash), b1 = b0 + m * hs;
+    const uintptr_t c0 = reinterpret_cast<uintptr_t>(pos), c1 = c0 + m * 4;
+    const uintptr_t d0 = reinterpret_cast<uintptr_t>(sorted_pos), d1 = d0 + m * 4;
+    if ((a0 < b1 && b0 < a1) || (c0 < d1 && d0 < c1)) return fail(SWS_ERR_INVALID, "inputs and outputs overlap");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool wide = hash_bits > 32;
+  const uint64_t kbytes = round_up(m * 8, 256), vbytes = wide ? round_up(m * 4, 256) : 0;
+  const uint64_t hbytes = round_up(sws::table_hist_words(m) * 4, 256);
+  const uint64_t bbytes = round_up(sws::table_bsum_words(m) * 4, 256);
+  const uint64_t gbytes = round_up(sws::table_gap_bytes(bucket_bits), 256);
+  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256;
+  s = ensure_ws(ctx, total, st);
+  if (s) return s;
+  char *w = static_cast<char *>(ctx->ws);
+  sws::TableArgs a{};
+  a.hash = hash;
+  a.pos = pos;
+  a.m = m;
+  a.hash_bits = hash_bits;
+  a.bucket_bits = bucket_bits;
+  a.sorted_hash = sorted_hash;
+  a.sorted_pos = sorted_pos;
+  a.offsets = bucket_offsets;
+  a.ws_keys[0] = reinterpret_cast<unsigned long long *>(w);
+  a.ws_keys[1] = reinterpret_cast<unsigned long long *>(w + kbytes);
+  a.ws_vals[0] = wide ? reinterpret_cast<uint32_t *>(w + 2 * kbytes) : nullptr;
+  a.ws_vals[1] = wide ? reinterpret_cast<uint32_t *>(w + 2 * kbytes + vbytes) : nullptr;
+  a.ws_hist = reinterpret_cast<uint32_t *>(w + 2 * kbytes + 2 * vbytes);
+  a.ws_bsum = reinterpret_cast<uint32_t *>(w + 2 * kbytes + 2 * vbytes + hbytes);
+  a.ws_gaps = w + 2 * kbytes + 2 * vbytes + hbytes + bbytes;
+  a.ws_ngaps = reinterpret_cast<unsigned long long *>(w + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes);
+  a.gap_cap = sws::table_gap_capacity(bucket_bits);
+  cudaError_t e = sws::launch_table(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "seed-table launch");
+  return SWS_OK;
+}
+
 }  // extern "C"

@@ -59,6 +59,30 @@ cudaError_t launch_pick_offsets_fixup(uint64_t *pick_offsets, uint64_t nreads, c
 // k-mer values.
 cudaError_t launch_kmers(const uint8_t *seq, uint64_t n, int k, int kind, void *out, int *err, cudaStream_t stream);
 
+// Seed table (radix sort + pointer table).
+struct TableArgs {
+  const void *hash;       // uint32 (hash_bits <= 32) or uint64
+  const uint32_t *pos;
+  uint64_t m;
+  int hash_bits, bucket_bits;
+  void *sorted_hash;
+  uint32_t *sorted_pos;
+  uint64_t *offsets;      // 2^bucket_bits + 1
+  // workspace
+  unsigned long long *ws_keys[2];
+  uint32_t *ws_vals[2];   // hash_bits > 32 only
+  uint32_t *ws_hist;      // table_hist_words(m)
+  uint32_t *ws_bsum;      // table_bsum_words(m)
+  void *ws_gaps;          // table_gap_bytes(bucket_bits)
+  unsigned long long *ws_ngaps;
+  uint64_t gap_cap;
+};
+uint64_t table_gap_capacity(int bucket_bits);
+uint64_t table_hist_words(uint64_t m);
+uint64_t table_bsum_words(uint64_t m);
+uint64_t table_gap_bytes(int bucket_bits);
+cudaError_t launch_table(const TableArgs &a, cudaStream_t stream);
+
 // Device error bits.
 enum DevErr { DEVERR_LOOKBACK_TIMEOUT = 1, DEVERR_COPY_TIMEOUT = 2 };
 
