@@ -139,6 +139,28 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
                                 uint64_t total_bases, int k, int w, int mode, void *hash_out, uint32_t *pos_out,
                                 uint64_t capacity, uint64_t *pick_offsets, uint64_t *count_out, void *stream);
 
+/* ---- minimizers without allocation ------------------------------------------------------ */
+/* The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory: code running inside a device-memory allocator's hooks (allocating there would
+ * re-enter the allocator), programs whose device memory is all handed out in advance by a
+ * framework that owns it, and latency-critical paths that must not pay for, or risk the failure
+ * of, an allocation.  It computes exactly what sws_minimizers computes (same arguments, same
+ * outputs, no N-block or key-mode difference), on the calling thread's current device, without a
+ * context and without calling cudaMalloc, cudaFree or any allocating routine.
+ *   Scratch: a fixed 4 MiB array in device global memory that the library declares, held by every
+ *     device that loads the library until the process exits.  It bounds the input: at most
+ *     262,128 tiles of (4096 - w) / 64 * 64 windows each (about 1.05e9 bases at w = 10); longer
+ *     inputs are rejected with SWS_ERR_INVALID before any work is queued.
+ *   Set-up: the first call on each device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   Sharing: every call uses the same array, so calls that overlap on the GPU (for example on two
+ *     streams at once) race and give wrong results; serialize them.
+ *   Faults: count_out is set to all ones when the call is queued; if a bounded device-side wait
+ *     runs out, the ordered output is not completed and count_out stays all ones. */
+sws_status sws_minimizers_noalloc(const uint8_t *seq, uint64_t n, int k, int w, int mode, const int64_t *nblocks,
+                                  uint64_t n_nblocks, void *hash_out, uint32_t *pos_out, uint64_t capacity,
+                                  uint64_t *count_out, void *stream);
+
 /* ---- seed table (Sec. 2.4, Fig. 1) -------------------------------------------------------- */
 /* Build the seed table from m (hash, position) hits: a position table listing the hits sorted by
  * hash, and a pointer table with, for every bucket b of hash values (bucket of h =

@@ -52,6 +52,7 @@ SIGNATURES = {
     "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
     "sws_minimizers_batch": (i32, [vp, vp, vp, u64, u64, i32, i32, i32, vp, vp, u64, vp, vp, vp]),
     "sws_kmer_table": (i32, [vp, vp, vp, u64, i32, i32, vp, vp, vp, vp]),
+    "sws_minimizers_noalloc": (i32, [vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
 }
 
 

@@ -103,6 +103,13 @@ sws_status check_mini_args(int k, int w, int mode) {
 
 }  // namespace
 
+namespace sws {
+// For other translation units: record an error message for sws_last_error().
+sws_status report_error(sws_status s, const char *msg) { return fail(s, "%s", msg); }
+// For other translation units: the argument checks of the minimizer entry points.
+sws_status check_minimizer_args(int k, int w, int mode) { return check_mini_args(k, w, mode); }
+}  // namespace sws
+
 extern "C" {
 
 const char *sws_last_error(void) { return g_err.c_str(); }

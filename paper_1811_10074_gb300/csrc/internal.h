@@ -83,6 +83,10 @@ uint64_t table_bsum_words(uint64_t m);
 uint64_t table_gap_bytes(int bucket_bits);
 cudaError_t launch_table(const TableArgs &a, cudaStream_t stream);
 
+// Error reporting and argument checks shared with api.cu (sws_status is an int).
+int report_error(int status, const char *msg);
+int check_minimizer_args(int k, int w, int mode);
+
 // Device error bits.
 enum DevErr { DEVERR_LOOKBACK_TIMEOUT = 1, DEVERR_COPY_TIMEOUT = 2 };
 
