@@ -215,6 +215,67 @@ sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int ki
   return SWS_OK;
 }
 
+// Workspace of the staged minimizer path: per-tile counts (+1 for the total), scan scratch, one
+// barrier summary per tile, then the staging slots (hash, position, and for read batches the read
+// index of a read's first pick), then `extra` bytes.
+struct StagedWs {
+  uint64_t counts_off, scan_off, tilebar_off, hash_off, pos_off, first_off, extra_off, total;
+};
+StagedWs staged_ws_layout(uint64_t tiles, int w, bool reads, uint64_t extra) {
+  StagedWs L;
+  const uint64_t slots = tiles * (uint64_t)sws::mini_fast_tile_windows(w);
+  L.counts_off = 0;
+  L.scan_off = round_up((tiles + 1) * 4, 256);
+  L.tilebar_off = L.scan_off + round_up(sws::scan_u32_scratch_words(tiles + 1) * 4, 256);
+  L.hash_off = L.tilebar_off + round_up(tiles * 8, 256);
+  L.pos_off = L.hash_off + round_up(slots * 4, 256);
+  L.first_off = L.pos_off + round_up(slots * 4, 256);
+  L.extra_off = L.first_off + (reads ? round_up(slots * 4, 256) : 0);
+  L.total = L.extra_off + round_up(extra, 256);
+  return L;
+}
+
+// Fill the workspace pointers of `a` and queue the minimizer kernels (staged path when it
+// applies, look-back path otherwise).  `extra` bytes of workspace are returned in *extra_ptr.
+sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrier, uint64_t nwin, uint64_t extra,
+                          void **extra_ptr, cudaStream_t st) {
+  const bool staged = sws::mini_fast_applies(source, a.k, a.w);
+  if (staged) {
+    const uint64_t tw = (uint64_t)sws::mini_fast_tile_windows(a.w);
+    const uint64_t tiles = (nwin + tw - 1) / tw;
+    if (tiles >= 0xffffffffull) return fail(SWS_ERR_INVALID, "input too long");
+    const StagedWs L = staged_ws_layout(tiles, a.w, barrier == sws::BAR_READS, extra);
+    sws_status s = ensure_ws(ctx, L.total, st);
+    if (s) return s;
+    char *w = static_cast<char *>(ctx->ws);
+    a.tile_counts = reinterpret_cast<uint32_t *>(w + L.counts_off);
+    a.scan_tmp = reinterpret_cast<uint32_t *>(w + L.scan_off);
+    a.tile_bar = reinterpret_cast<uint2 *>(w + L.tilebar_off);
+    a.stg_hash = reinterpret_cast<uint32_t *>(w + L.hash_off);
+    a.stg_pos = reinterpret_cast<uint32_t *>(w + L.pos_off);
+    a.stg_first = reinterpret_cast<uint32_t *>(w + L.first_off);
+    a.err = ctx->d_err;
+    if (extra_ptr) *extra_ptr = w + L.extra_off;
+    cudaError_t e = sws::launch_minimizers_staged(a, source, barrier, tiles, st);
+    if (e != cudaSuccess) return cuda_fail(e, "staged minimizer launch");
+    return SWS_OK;
+  }
+  const uint64_t tiles = sws::mini_lookback_tiles(nwin, a.w);
+  const MiniWs L = mini_ws_layout(tiles, extra);
+  sws_status s = ensure_ws(ctx, L.total, st);
+  if (s) return s;
+  char *w = static_cast<char *>(ctx->ws);
+  SWS_CUDA(cudaMemsetAsync(w, 0, L.tilebar_off, st));
+  a.status = reinterpret_cast<unsigned long long *>(w);
+  a.tile_counter = reinterpret_cast<unsigned int *>(w + L.counter_off);
+  a.tile_bar = reinterpret_cast<uint2 *>(w + L.tilebar_off);
+  a.err = ctx->d_err;
+  if (extra_ptr) *extra_ptr = w + L.extra_off;
+  cudaError_t e = sws::launch_minimizers_lookback(a, source, barrier, tiles, st);
+  if (e != cudaSuccess) return cuda_fail(e, "minimizer launch");
+  return SWS_OK;
+}
+
 static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq, const uint32_t *keys, uint64_t n,
                                     int k, int w, int mode, const int64_t *nblocks, uint64_t n_nblocks,
                                     void *hash_out, uint32_t *pos_out, uint64_t capacity, uint64_t *count_out,
@@ -230,18 +291,12 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t span = source == sws::SRC_DNA ? (uint64_t)(w + k - 1) : (uint64_t)w;
   const uint64_t nwin = n >= span ? n - span + 1 : 0;
-  const uint64_t tiles = sws::mini_num_tiles(nwin, w);
-  if (tiles == 0) {
+  if (nwin == 0) {
     SWS_CUDA(cudaMemsetAsync(count_out, 0, sizeof(uint64_t), st));
     return SWS_OK;
   }
   if (source == sws::SRC_DNA && !seq) return fail(SWS_ERR_INVALID, "seq is NULL");
   if (source == sws::SRC_KEYS && !keys) return fail(SWS_ERR_INVALID, "keys is NULL");
-  const MiniWs L = mini_ws_layout(tiles, 0);
-  s = ensure_ws(ctx, L.total, st);
-  if (s) return s;
-  char *ws = static_cast<char *>(ctx->ws);
-  SWS_CUDA(cudaMemsetAsync(ws, 0, L.tilebar_off, st));
   sws::MiniArgs a{};
   a.seq = seq;
   a.keys = keys;
@@ -255,13 +310,7 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
   a.pos_out = pos_out;
   a.capacity = capacity;
   a.count_out = count_out;
-  a.status = reinterpret_cast<unsigned long long *>(ws);
-  a.tile_counter = reinterpret_cast<unsigned int *>(ws + L.counter_off);
-  a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar_off);
-  a.err = ctx->d_err;
-  cudaError_t e = sws::launch_minimizers(a, source, sws::BAR_NBLOCK, tiles, st);
-  if (e != cudaSuccess) return cuda_fail(e, "minimizer launch");
-  return SWS_OK;
+  return run_minimizers(ctx, a, source, sws::BAR_NBLOCK, nwin, 0, nullptr, st);
 }
 
 sws_status sws_minimizers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
@@ -291,19 +340,12 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t span = (uint64_t)(w + k - 1);
   const uint64_t nwin = total_bases >= span ? total_bases - span + 1 : 0;
-  const uint64_t tiles = nreads > 0 ? sws::mini_num_tiles(nwin, w) : 0;
-  if (tiles == 0) {
+  if (nreads == 0 || nwin == 0) {
     SWS_CUDA(cudaMemsetAsync(count_out, 0, sizeof(uint64_t), st));
     SWS_CUDA(cudaMemsetAsync(pick_offsets, 0, (nreads + 1) * sizeof(uint64_t), st));
     return SWS_OK;
   }
   if (!seq) return fail(SWS_ERR_INVALID, "seq is NULL");
-  const uint64_t fix_blocks = (nreads + 1023) / 1024 + 1;
-  const MiniWs L = mini_ws_layout(tiles, fix_blocks * 8);
-  s = ensure_ws(ctx, L.total, st);
-  if (s) return s;
-  char *ws = static_cast<char *>(ctx->ws);
-  SWS_CUDA(cudaMemsetAsync(ws, 0, L.tilebar_off, st));
   SWS_CUDA(cudaMemsetAsync(pick_offsets, 0xff, (nreads + 1) * sizeof(uint64_t), st));
   sws::MiniArgs a{};
   a.seq = seq;
@@ -318,14 +360,11 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
   a.capacity = capacity;
   a.count_out = count_out;
   a.pick_offsets = pick_offsets;
-  a.status = reinterpret_cast<unsigned long long *>(ws);
-  a.tile_counter = reinterpret_cast<unsigned int *>(ws + L.counter_off);
-  a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar_off);
-  a.err = ctx->d_err;
-  cudaError_t e = sws::launch_minimizers(a, sws::SRC_DNA, sws::BAR_READS, tiles, st);
-  if (e != cudaSuccess) return cuda_fail(e, "batched minimizer launch");
-  e = sws::launch_pick_offsets_fixup(pick_offsets, nreads, count_out,
-                                     reinterpret_cast<uint64_t *>(ws + L.extra_off), st);
+  const uint64_t fix_blocks = (nreads + 1023) / 1024 + 1;
+  void *fix = nullptr;
+  s = run_minimizers(ctx, a, sws::SRC_DNA, sws::BAR_READS, nwin, fix_blocks * 8, &fix, st);
+  if (s) return s;
+  cudaError_t e = sws::launch_pick_offsets_fixup(pick_offsets, nreads, count_out, static_cast<uint64_t *>(fix), st);
   if (e != cudaSuccess) return cuda_fail(e, "pick-offset fix-up launch");
   return SWS_OK;
 }

@@ -42,17 +42,36 @@ struct MiniArgs {
   unsigned int *tile_counter;  // zeroed before the launch
   uint2 *tile_bar;             // one word per tile (filled by the launcher when barriers exist)
   int *err;                    // device error word of the context
+  // staged path only
+  uint32_t *tile_counts;  // [num_tiles + 1], exclusive offsets after the scan
+  uint32_t *scan_tmp;     // scan_u32_scratch_words(num_tiles + 1)
+  uint32_t *stg_hash;     // [num_tiles * windows per tile]
+  uint32_t *stg_pos;
+  uint32_t *stg_first;    // read batches: read index of a read's first pick, else ~0
 };
 
 enum MiniSource { SRC_DNA = 0, SRC_KEYS = 1 };
 enum MiniBarrier { BAR_NBLOCK = 0, BAR_READS = 1 };
 
-// Windows per tile for a given w (a multiple of 64), 0 if w is too large.
-int mini_tile_windows(int w);
-// Number of tiles of a launch over `nwin` window positions (nwin may be 0).
-uint64_t mini_num_tiles(uint64_t nwin, int w);
-// Queue the minimizer kernel; workspace words must already be zeroed on `stream`.
-cudaError_t launch_minimizers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, cudaStream_t stream);
+// Look-back path (any w <= 4000, any k): one kernel, picks placed in order by a decoupled
+// look-back over per-tile status words (zeroed, with the tile counter, before the launch).
+int mini_tile_windows(int w);  // windows per tile (a multiple of 64), 0 if w is too large
+uint64_t mini_lookback_tiles(uint64_t nwin, int w);
+cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
+                                       cudaStream_t stream);
+// Staged path (w in 4..16, keys of at most 32 bits): a persistent kernel writes each tile's picks
+// to a fixed slot, a scan of the per-tile counts gives offsets, a gather puts picks in order.
+bool mini_fast_applies(int source, int k, int w);
+int mini_fast_tile_windows(int w);
+cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
+                                     cudaStream_t stream);
+// The per-tile summary of the barriers (N-blocks or read starts) that can touch each tile.
+bool tile_barriers_needed(const MiniArgs &a, int source, int barrier);
+cudaError_t launch_tile_barriers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, int TW, int span,
+                                 cudaStream_t stream);
+// Exclusive scan of uint32 counts in place (scratch of scan_u32_scratch_words(len) words).
+uint64_t scan_u32_scratch_words(uint64_t len);
+cudaError_t scan_u32(uint32_t *a, uint64_t len, uint32_t *bsum, cudaStream_t stream);
 // Batch fix-up: reads without picks get the offset of the next read that has some.
 cudaError_t launch_pick_offsets_fixup(uint64_t *pick_offsets, uint64_t nreads, const uint64_t *count,
                                       uint64_t *scratch, cudaStream_t stream);

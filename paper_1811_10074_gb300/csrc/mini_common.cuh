@@ -1,0 +1,308 @@
+// mini_common.cuh -- device pieces shared by the minimizer kernels: TMA bulk staging of packed
+// bases (cp.async.bulk completed on an mbarrier, bounded waits), k-mer arithmetic on the packed
+// bit stream, Wang's mix, minimizer keys, and the decoupled look-back over per-tile counts.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "../../include/sws.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace sws {
+namespace mini {
+
+constexpr unsigned long long FLAG_AGG = 1ull << 62;
+constexpr unsigned long long FLAG_INC = 2ull << 62;
+constexpr unsigned long long FLAG_ERR = 3ull << 62;
+constexpr unsigned long long VALUE_MASK = (1ull << 62) - 1;
+constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;  // x >= 64 ns sleep: about a second at most
+constexpr int COPY_SPIN_LIMIT = 1 << 22;
+
+// ---- PTX helpers ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One-dimensional TMA copy global -> shared (16-byte aligned addresses, size multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  return v;
+}
+
+// Stage bytes [gb0, gb0 + sbytes) of the packed sequence into shared memory (zeros outside
+// [0, nbytes)).  The 16-byte-aligned interior goes by one TMA bulk copy completed on an
+// mbarrier; the ragged edge bytes are loaded by the threads.  Returns false (and records the
+// fault) if the copy did not complete within the spin limit.
+__device__ inline bool stage_bytes(uint8_t *sdst, const uint8_t *__restrict__ seq, uint64_t nbytes, long long gb0,
+                            int sbytes, unsigned long long *bar, int *err) {
+  const long long lo = gb0 > 0 ? gb0 : 0;
+  long long hi = gb0 + sbytes;
+  if (hi > (long long)nbytes) hi = (long long)nbytes;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(seq) & 15u) == 0);
+  const long long bulk = (aligned && hi > lo) ? ((hi - lo) & ~15ll) : 0;
+  if (threadIdx.x == 0 && bulk > 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, (uint32_t)bulk);
+    bulk_g2s(sdst + (lo - gb0), seq + lo, (uint32_t)bulk, bar);
+  }
+  for (int b = threadIdx.x; b < sbytes; b += blockDim.x) {
+    const long long g = gb0 + b;
+    if (g >= lo && g < lo + bulk) continue;
+    sdst[b] = (g >= 0 && g < (long long)nbytes) ? seq[g] : (uint8_t)0;
+  }
+  __syncthreads();
+  bool ok = true;
+  if (bulk > 0) {
+    int spins = 0;
+    while (!mbar_try_wait(bar, 0)) {
+      if (++spins > COPY_SPIN_LIMIT) {
+        ok = false;
+        break;
+      }
+      __nanosleep(32);
+    }
+    if (!ok) {
+      atomicOr(err, DEVERR_COPY_TIMEOUT);
+      // give the copy one more bounded chance to land before the CTA can exit
+      for (int s = 0; s < COPY_SPIN_LIMIT && !mbar_try_wait(bar, 0); ++s) __nanosleep(64);
+    }
+  }
+  return ok;
+}
+
+// ---- k-mer arithmetic -----------------------------------------------------------------------
+// Wang's 64-bit integer mix, written in its multiplicative form, truncated to the mask m after
+// every step (a bijection on [0, m]).
+__device__ __forceinline__ uint32_t wang_mix32(uint32_t x, uint32_t m) {
+  x = (x * 0x1FFFFFu + 0xFFFFFFFFu) & m;  // (x << 21) - x - 1
+  x ^= x >> 24;
+  x = (x * 265u) & m;
+  x ^= x >> 14;
+  x = (x * 21u) & m;
+  x ^= x >> 28;
+  x = (x * 0x80000001u) & m;
+  return x;
+}
+__device__ __forceinline__ unsigned long long wang_mix64(unsigned long long x, unsigned long long m) {
+  x = (x * 0x1FFFFFull + 0xFFFFFFFFFFFFFFFFull) & m;
+  x ^= x >> 24;
+  x = (x * 265ull) & m;
+  x ^= x >> 14;
+  x = (x * 21ull) & m;
+  x ^= x >> 28;
+  x = (x * 0x80000001ull) & m;
+  return x;
+}
+// Reverse the order of the 2-bit groups of a word.
+__device__ __forceinline__ uint32_t rev_pairs32(uint32_t x) {
+  x = __brev(x);
+  return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+__device__ __forceinline__ unsigned long long rev_pairs64(unsigned long long x) {
+  x = __brevll(x);
+  return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+// (fwd, rc, canonical, hash, key-value) of one k-mer from the bases in the low bits of x.
+struct Kmer32 {
+  uint32_t fwd, rc;
+};
+__device__ __forceinline__ Kmer32 kmer32(uint32_t x, int k, uint32_t kmask) {
+  Kmer32 r;
+  r.rc = ~x & kmask;
+  r.fwd = rev_pairs32(x) >> (32 - 2 * k);
+  return r;
+}
+struct Kmer64 {
+  unsigned long long fwd, rc;
+};
+__device__ __forceinline__ Kmer64 kmer64(unsigned long long x, int k, unsigned long long kmask) {
+  Kmer64 r;
+  r.rc = ~x & kmask;
+  r.fwd = rev_pairs64(x) >> (64 - 2 * k);
+  return r;
+}
+__device__ __forceinline__ uint32_t key_value32(const Kmer32 &q, int mode, uint32_t kmask) {
+  if (mode == SWS_MINI_FWD) return q.fwd;
+  const uint32_t c = q.fwd < q.rc ? q.fwd : q.rc;
+  return mode == SWS_MINI_CANONICAL ? c : wang_mix32(c, kmask);
+}
+__device__ __forceinline__ unsigned long long key_value64(const Kmer64 &q, int mode, unsigned long long kmask) {
+  if (mode == SWS_MINI_FWD) return q.fwd;
+  const unsigned long long c = q.fwd < q.rc ? q.fwd : q.rc;
+  return mode == SWS_MINI_CANONICAL ? c : wang_mix64(c, kmask);
+}
+
+// ---- keys -----------------------------------------------------------------------------------
+template <class KOp>
+struct KeyTraits;
+template <>
+struct KeyTraits<OpMinKey64> {
+  using T = unsigned long long;
+  static __device__ __forceinline__ T make(unsigned long long h, uint32_t pos) { return (h << 32) | pos; }
+  static __device__ __forceinline__ uint32_t pos(T k) { return (uint32_t)k; }
+  static __device__ __forceinline__ unsigned long long hash(T k) { return k >> 32; }
+  static __device__ __forceinline__ T none() { return ~0ull; }
+};
+template <>
+struct KeyTraits<OpMinKey96> {
+  using T = Key96;
+  static __device__ __forceinline__ T make(unsigned long long h, uint32_t pos) {
+    return Key96{(uint32_t)h, (uint32_t)(h >> 32), pos};
+  }
+  static __device__ __forceinline__ uint32_t pos(T k) { return k.pos; }
+  static __device__ __forceinline__ unsigned long long hash(T k) { return OpMinKey96::h(k); }
+  static __device__ __forceinline__ T none() { return OpMinKey96::identity(); }
+};
+
+// Warp-level look-back (warp 0 of a CTA): 32 predecessors per poll.  Returns the number of picks
+// of all earlier tiles; sets `failed` if a wait ran out or an earlier tile failed.
+__device__ inline unsigned long long lookback_warp(unsigned long long *status, uint32_t tile, unsigned long long agg,
+                                                   int *err, bool &failed) {
+  const int lane = threadIdx.x & 31;
+  failed = false;
+  if (tile == 0) {
+    if (lane == 0) st_relaxed(&status[0], FLAG_INC | agg);
+    return 0;
+  }
+  if (lane == 0) st_relaxed(&status[tile], FLAG_AGG | agg);
+  unsigned long long excl = 0;
+  long long base = (long long)tile - 1;
+  while (true) {
+    const long long idx = base - lane;
+    unsigned long long s = FLAG_INC;
+    int spins = 0;
+    while (true) {
+      s = idx >= 0 ? ld_relaxed(&status[idx]) : FLAG_INC;
+      if (__all_sync(kFull, (s >> 62) != 0ull)) break;
+      if (++spins > LOOKBACK_SPIN_LIMIT) {
+        failed = true;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (failed) break;
+    if (__ballot_sync(kFull, (s >> 62) == 3ull)) {
+      failed = true;
+      break;
+    }
+    const unsigned inc = __ballot_sync(kFull, (s >> 62) == 2ull);
+    unsigned long long v = s & VALUE_MASK;
+    if (inc) {
+      if (lane > __ffs(inc) - 1) v = 0;
+      excl += warp_sum_u64(v);
+      break;
+    }
+    excl += warp_sum_u64(v);
+    base -= 32;
+  }
+  if (lane == 0) {
+    if (failed) {
+      st_relaxed(&status[tile], FLAG_ERR);
+      atomicOr(err, DEVERR_LOOKBACK_TIMEOUT);
+    } else {
+      st_relaxed(&status[tile], FLAG_INC | (excl + agg));
+    }
+  }
+  return excl;
+}
+
+// CTA-wide look-back: every thread polls one predecessor, so each round trip to L2 inspects
+// blockDim.x tiles and the frontier of known inclusive prefixes advances that many tiles per
+// round trip (a warp-wide look-back advances it by only 32).  All threads of the CTA must call
+// it; `red` is shared scratch of at least 2 * (blockDim.x / 32) + 2 words.  Returns the number of
+// picks of all earlier tiles; sets `failed` when a bounded wait ran out or an earlier tile failed.
+__device__ inline unsigned long long lookback_cta(unsigned long long *status, uint32_t tile,
+                                                  unsigned long long agg, int *err, bool &failed,
+                                                  unsigned long long *red) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  failed = false;
+  if (tile == 0) {
+    if (t == 0) st_relaxed(&status[0], FLAG_INC | agg);
+    return 0;
+  }
+  if (t == 0) st_relaxed(&status[tile], FLAG_AGG | agg);
+  unsigned long long excl = 0;
+  long long base = (long long)tile - 1;
+  while (true) {
+    const long long idx = base - t;
+    unsigned long long s = idx >= 0 ? ld_relaxed(&status[idx]) : FLAG_INC;
+    int spins = 0;
+    while (!__syncthreads_and((s >> 62) != 0ull)) {
+      if (++spins > LOOKBACK_SPIN_LIMIT) {
+        failed = true;
+        break;
+      }
+      __nanosleep(64);
+      if ((s >> 62) == 0ull) s = ld_relaxed(&status[idx]);
+    }
+    if (failed) break;
+    if (__syncthreads_or((s >> 62) == 3ull)) {
+      failed = true;
+      break;
+    }
+    // the nearest predecessor holding an inclusive prefix
+    const unsigned inc = __ballot_sync(kFull, (s >> 62) == 2ull);
+    if (lane == 0) red[warp] = inc ? (unsigned long long)(warp * 32 + __ffs(inc) - 1) : ~0ull;
+    __syncthreads();
+    unsigned long long first = ~0ull;
+    for (int i = 0; i < nw; ++i) first = red[i] < first ? red[i] : first;
+    unsigned long long v = (first == ~0ull || (unsigned long long)t <= first) ? (s & VALUE_MASK) : 0ull;
+    v = warp_sum_u64(v);
+    if (lane == 0) red[nw + warp] = v;
+    __syncthreads();
+    for (int i = 0; i < nw; ++i) excl += red[nw + i];
+    __syncthreads();
+    if (first != ~0ull) break;
+    base -= blockDim.x;
+  }
+  if (t == 0) {
+    if (failed) {
+      st_relaxed(&status[tile], FLAG_ERR);
+      atomicOr(err, DEVERR_LOOKBACK_TIMEOUT);
+    } else {
+      st_relaxed(&status[tile], FLAG_INC | (excl + agg));
+    }
+  }
+  return excl;
+}
+
+}  // namespace mini
+}  // namespace sws

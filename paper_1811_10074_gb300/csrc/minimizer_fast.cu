@@ -1,0 +1,465 @@
+// minimizer_fast.cu -- minimizers for window lengths w = 4..16 with keys of at most 32 bits
+// (k <= 16, or precomputed 32-bit keys), in three steps that never wait on one another inside a
+// kernel:
+//
+//   1. k_mini_stage (persistent, one CTA per resident slot, tiles assigned statically): keys of a
+//      tile's k-mers, the least key of every window (Sec. 2.4) by block-combine, which windows
+//      store a new pick, and where; the tile's picks go to a fixed slot of a staging area and the
+//      count to a per-tile word.  The next tile's packed bases are fetched by TMA (cp.async.bulk
+//      into the other of two shared buffers, completed on an mbarrier) while this one computes.
+//   2. an exclusive scan of the per-tile counts (scan_u32 in table.cu);
+//   3. k_mini_gather: each warp copies one tile's picks to their final, position-ordered place.
+//
+// The staging costs about 16 bytes of traffic per pick; in exchange no CTA ever waits for another
+// (the single-kernel path in minimizer.cu orders its output with a look-back instead).
+//
+// Details of step 1:
+// * A tile starts at a multiple of w and a thread owns VPT = w * floor(16 / w) consecutive k-mers,
+//   so the blocks of w are whole, compile-time groups of registers: the block-combine (in-block
+//   suffix minimum with the next block's prefix minimum) needs no segment bookkeeping and runs on
+//   32-bit values, one min per step.
+// * Ties.  Keys are ordered by (value, position).  Instead of 64-bit keys, the scans carry a 32-bit
+//   value and the position of its leftmost occurrence: a prefix step takes the new element only
+//   when strictly smaller, a suffix step when smaller or equal, and a window's suffix part (left)
+//   wins ties against its prefix part (right).  Every window then knows its pick's position, and a
+//   window stores a pick when its position differs from the previous window's.
+#include <cstdio>
+
+#include "../../include/sws.h"
+#include "common.cuh"
+#include "internal.h"
+#include "mini_common.cuh"
+
+namespace sws {
+
+using namespace mini;
+
+namespace {
+
+constexpr int FNT = 256;
+constexpr int FNW = FNT / 32;
+constexpr int FMAXB = 128;
+
+template <int W, int SRC, int BAR>
+struct Geo {
+  static constexpr int NB = 16 / W;              // blocks of w per thread
+  static constexpr int VPT = W * NB;             // k-mers per thread
+  static constexpr int L = FNT * VPT;            // k-mers per tile
+  static constexpr int TW = (FNT * NB - 2) * W;  // windows per tile (a multiple of w)
+  static constexpr int STAGE = SRC == SRC_DNA ? ((63 + L + 16) / 4 + 16 + 15) / 16 * 16 : (L + 8) * 4;
+  static constexpr int OFF_SX = 2 * STAGE;  // keys of the tile: sx[o + 1]
+  static constexpr int OFF_BAR = OFF_SX + ((L + 2) * 4 + 15) / 16 * 16;
+  static constexpr int OFF_PICKS = OFF_BAR + FMAXB * 16;
+  static constexpr int PICK_WORDS = BAR == BAR_READS ? 3 : 2;
+  static constexpr int BYTES = OFF_PICKS + TW * 4 * PICK_WORDS;
+};
+
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+  return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+struct Staging {
+  long long gb0;   // global byte of staged byte 0
+  long long lo;    // first byte of the bulk copy
+  long long bulk;  // bytes of the bulk copy (0: none)
+};
+
+template <int W, int BAR, int SRC>
+__global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, int span,
+                                                    const uint2 *__restrict__ tile_bar, uint32_t num_tiles) {
+  using G = Geo<W, SRC, BAR>;
+  constexpr int VPT = G::VPT, NB = G::NB, WM1 = W > 1 ? W - 1 : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *sx = reinterpret_cast<uint32_t *>(smem + G::OFF_SX);
+  long long *sbar = reinterpret_cast<long long *>(smem + G::OFF_BAR);
+  uint32_t *sh_hash = reinterpret_cast<uint32_t *>(smem + G::OFF_PICKS);
+  uint32_t *sh_pos = sh_hash + G::TW;
+  uint32_t *sh_first = sh_pos + G::TW;  // read batches only
+  __shared__ unsigned long long s_mbar[2];
+  __shared__ Staging s_st[2];
+  __shared__ uint32_t s_wcount[FNW];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint8_t *src = SRC == SRC_DNA ? a.seq : reinterpret_cast<const uint8_t *>(a.keys);
+  const uint64_t nbytes = SRC == SRC_DNA ? (a.n + 3) / 4 : a.n * 4;
+  const bool src_aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+
+  // Thread 0: start the bulk copy of tile `tile`'s bases (or keys) into buffer b.
+  auto issue = [&](int b, uint32_t tile) {
+    const long long i0 = (long long)tile * G::TW - W;
+    const long long gb0 = SRC == SRC_DNA ? floor_div(i0, 64) * 16 : floor_div(i0, 4) * 16;
+    const long long lo = gb0 > 0 ? gb0 : 0;
+    long long hi = gb0 + G::STAGE;
+    if (hi > (long long)nbytes) hi = (long long)nbytes;
+    const long long bulk = (src_aligned && hi > lo) ? ((hi - lo) & ~15ll) : 0;
+    s_st[b] = Staging{gb0, lo, bulk};
+    if (bulk > 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&s_mbar[b], (uint32_t)bulk);
+      bulk_g2s(smem + b * G::STAGE + (lo - gb0), src + lo, (uint32_t)bulk, &s_mbar[b]);
+    }
+  };
+
+  if (t == 0) {
+    mbar_init(&s_mbar[0], 1);
+    mbar_init(&s_mbar[1], 1);
+    fence_mbar_init();
+    if (blockIdx.x < num_tiles) issue(0, blockIdx.x);
+    if (blockIdx.x == 0) a.tile_counts[num_tiles] = 0;  // the scan's last entry becomes the total
+  }
+  __syncthreads();
+  unsigned phases = 0u;  // bit b: parity of the next completion of buffer b's mbarrier
+
+  int it = 0;
+  for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    if (t == 0 && tile + gridDim.x < num_tiles) issue(b ^ 1, tile + gridDim.x);
+    const long long p0 = (long long)tile * G::TW;  // first window of the tile
+    const long long i0 = p0 - W;                   // k-mer (and window) of local index 0
+    uint8_t *stage = smem + b * G::STAGE;
+
+    // ---- bases (or keys) of this tile in shared memory; barriers that can touch it ------------
+    const Staging stg = s_st[b];
+    bool ok = true;
+    if (stg.bulk > 0) {
+      const uint32_t ph = (phases >> b) & 1u;
+      int spins = 0;
+      while (!mbar_try_wait(&s_mbar[b], ph)) {
+        if (++spins > COPY_SPIN_LIMIT) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (!ok) {
+        if (t == 0) atomicOr(a.err, DEVERR_COPY_TIMEOUT);
+        for (int s = 0; s < COPY_SPIN_LIMIT && !mbar_try_wait(&s_mbar[b], ph); ++s) __nanosleep(64);
+      }
+      phases ^= 1u << b;
+    }
+    for (int i = t; i < G::STAGE; i += FNT) {
+      const long long g = stg.gb0 + i;
+      if (g >= stg.lo && g < stg.lo + stg.bulk) continue;
+      stage[i] = (g >= 0 && g < (long long)nbytes) ? src[g] : (uint8_t)0;
+    }
+    uint32_t g_lo = 0, nb = 0;
+    if (tile_bar != nullptr) {
+      const uint2 tb = tile_bar[tile];
+      g_lo = tb.x;
+      nb = tb.y;
+    }
+    const bool bar_in_smem = nb <= (uint32_t)FMAXB;
+    if (bar_in_smem) {
+      for (uint32_t i = t; i < nb; i += FNT) {
+        if (BAR == BAR_NBLOCK) {
+          sbar[2 * i] = a.bar[2 * (g_lo + i)];
+          sbar[2 * i + 1] = a.bar[2 * (g_lo + i) + 1];
+        } else {
+          const long long s = a.bar[g_lo + i + 1];
+          sbar[2 * i] = s;
+          sbar[2 * i + 1] = s;
+        }
+      }
+    }
+    __syncthreads();
+    auto bar_start = [&](uint32_t i) -> long long {
+      if (bar_in_smem) return sbar[2 * i];
+      return BAR == BAR_NBLOCK ? a.bar[2 * (g_lo + i)] : a.bar[g_lo + i + 1];
+    };
+    auto bar_end = [&](uint32_t i) -> long long {
+      if (bar_in_smem) return sbar[2 * i + 1];
+      return BAR == BAR_NBLOCK ? a.bar[2 * (g_lo + i) + 1] : a.bar[g_lo + i + 1];
+    };
+
+    // ---- keys (32-bit values) ------------------------------------------------------------------
+    const long long ifirst = i0 + (long long)t * VPT;
+    const long long tlo = p0 - 1, thi = p0 + G::TW - 1;  // windows this tile looks at
+    const bool interior = nb == 0 && tlo >= 0 && (unsigned long long)thi < nwin;
+    const long long lastv = (long long)a.n - (SRC == SRC_DNA ? a.k : 1);  // last valid k-mer
+    const int jlo = interior ? 0 : (ifirst < 0 ? (int)(-ifirst < VPT ? -ifirst : VPT) : 0);
+    const int jhi = interior ? VPT : (lastv < ifirst ? 0 : (int)(lastv - ifirst + 1 < VPT ? lastv - ifirst + 1 : VPT));
+    uint32_t x[VPT];
+    if (SRC == SRC_DNA) {
+      const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage);
+      const int r = (int)(i0 - 4 * stg.gb0) + t * VPT;  // staged base of this thread's first k-mer
+      const int q = r >> 4, s = (r & 15) * 2;
+      const uint32_t v0 = __funnelshift_r(sw[q], sw[q + 1], s);
+      const uint32_t v1 = __funnelshift_r(sw[q + 1], sw[q + 2], s);
+      const int k = a.k;
+      const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const uint32_t v = key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), a.mode, kmask);
+        x[j] = (j >= jlo && j < jhi) ? v : 0xFFFFFFFFu;
+      }
+    } else {
+      const uint32_t *sk = reinterpret_cast<const uint32_t *>(stage);
+      const int r = (int)(i0 - stg.gb0 / 4) + t * VPT;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) x[j] = (j >= jlo && j < jhi) ? sk[r + j] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
+    __syncthreads();
+
+    // ---- window minima and their leftmost positions, by block-combine on registers -----------
+    // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
+    // on ties (strict <), suffix minima the earliest too (<=); a window's suffix part lies left of
+    // its prefix part, so ties between the two go to the suffix.
+    uint32_t xn[WM1];  // the next thread's first w-1 keys
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i) xn[i] = sx[1 + (t + 1 < FNT ? t + 1 : t) * VPT + i];
+    const uint32_t xprev = sx[t * VPT];  // key of k-mer ifirst - 1 (unused for thread 0)
+    const int o0 = t * VPT;
+    uint32_t P[VPT], S[VPT], Pp[VPT], Sp[VPT], Pn[WM1], Pnp[WM1], y[VPT], yp[VPT];
+#pragma unroll
+    for (int b2 = 0; b2 < NB; ++b2) {
+      P[b2 * W] = x[b2 * W];
+      Pp[b2 * W] = o0 + b2 * W;
+#pragma unroll
+      for (int i = 1; i < W; ++i) {
+        const int j = b2 * W + i;
+        const bool c = x[j] < P[j - 1];
+        P[j] = c ? x[j] : P[j - 1];
+        Pp[j] = c ? (uint32_t)(o0 + j) : Pp[j - 1];
+      }
+      S[b2 * W + W - 1] = x[b2 * W + W - 1];
+      Sp[b2 * W + W - 1] = o0 + b2 * W + W - 1;
+#pragma unroll
+      for (int i = W - 2; i >= 0; --i) {
+        const int j = b2 * W + i;
+        const bool c = x[j] <= S[j + 1];
+        S[j] = c ? x[j] : S[j + 1];
+        Sp[j] = c ? (uint32_t)(o0 + j) : Sp[j + 1];
+      }
+    }
+    if (W > 1) {
+      Pn[0] = xn[0];
+      Pnp[0] = o0 + VPT;
+#pragma unroll
+      for (int i = 1; i < W - 1; ++i) {
+        const bool c = xn[i] < Pn[i - 1];
+        Pn[i] = c ? xn[i] : Pn[i - 1];
+        Pnp[i] = c ? (uint32_t)(o0 + VPT + i) : Pnp[i - 1];
+      }
+    }
+#pragma unroll
+    for (int b2 = 0; b2 < NB; ++b2) {
+      y[b2 * W] = S[b2 * W];
+      yp[b2 * W] = Sp[b2 * W];
+#pragma unroll
+      for (int i = 1; i < W; ++i) {
+        const int j = b2 * W + i;
+        const uint32_t pr = (b2 + 1 < NB) ? P[(b2 + 1) * W + i - 1] : Pn[i - 1];
+        const uint32_t prp = (b2 + 1 < NB) ? Pp[(b2 + 1) * W + i - 1] : Pnp[i - 1];
+        const bool c = S[j] <= pr;
+        y[j] = c ? S[j] : pr;
+        yp[j] = c ? Sp[j] : prp;
+      }
+    }
+    // pick of the window just before this thread's first: k-mer ifirst-1 and this block's first w-1
+    const uint32_t ypprev = W > 1 ? (xprev <= P[W > 1 ? W - 2 : 0] ? (uint32_t)(o0 - 1) : Pp[W > 1 ? W - 2 : 0])
+                                  : (uint32_t)(o0 - 1);
+
+    // ---- window validity -------------------------------------------------------------------------
+    unsigned vmask;
+    bool pvalid;
+    uint32_t qj[BAR == BAR_READS ? VPT : 1];  // barrier index of each window (read batches)
+    if (interior) {
+      vmask = (1u << VPT) - 1u;
+      pvalid = true;
+#pragma unroll
+      for (int j = 0; j < (BAR == BAR_READS ? VPT : 1); ++j) qj[j] = 0;
+    } else {
+      uint32_t q = 0, hi = nb;
+      const long long pf = ifirst - 1;
+      while (q < hi) {
+        const uint32_t mid = (q + hi) >> 1;
+        if (bar_end(mid) > pf) hi = mid;
+        else q = mid + 1;
+      }
+      auto valid_at = [&](long long p, uint32_t qq) {
+        const bool in_range = p >= 0 && (unsigned long long)p < nwin;
+        const bool clear = (qq == nb) || (bar_start(qq) > p + span - 1);
+        return in_range && clear;
+      };
+      pvalid = valid_at(pf, q);
+      vmask = 0;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const long long p = ifirst + j;
+        while (q < nb && bar_end(q) <= p) ++q;
+        if (BAR == BAR_READS) qj[BAR == BAR_READS ? j : 0] = q;
+        vmask |= (unsigned)valid_at(p, q) << j;
+      }
+    }
+    if (!ok) {
+      vmask = 0;
+      pvalid = false;
+    }
+
+    // ---- windows that store a pick: valid, and the previous window invalid or picked elsewhere ---
+    unsigned emask = 0, firstmask = 0;
+    {
+      bool pv = pvalid;
+      uint32_t pp = ypprev;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const int o = o0 + j;
+        const bool v = (vmask >> j) & 1u;
+        const bool e = v && o >= W && o < W + G::TW && (!pv || yp[j] != pp);
+        emask |= (unsigned)e << j;
+        firstmask |= (unsigned)(e && !pv) << j;
+        pv = v;
+        pp = yp[j];
+      }
+    }
+    const uint32_t cnt = __popc(emask);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += u;
+    }
+    if (lane == 31) s_wcount[warp] = inc;
+    __syncthreads();
+    uint32_t woff = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < FNW; ++i) {
+      const uint32_t c = s_wcount[i];
+      if (i < warp) woff += c;
+      total += c;
+    }
+    {
+      uint32_t r = woff + inc - cnt;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        if ((emask >> j) & 1u) {
+          uint32_t pos = (uint32_t)(i0 + (long long)yp[j]);
+          if (BAR == BAR_READS) {
+            const uint32_t rd = g_lo + qj[BAR == BAR_READS ? j : 0];
+            pos = (uint32_t)((long long)pos - a.bar[rd]);
+            sh_first[r] = ((firstmask >> j) & 1u) ? rd : 0xFFFFFFFFu;
+          }
+          sh_hash[r] = y[j];
+          sh_pos[r] = pos;
+          ++r;
+        }
+      }
+    }
+    __syncthreads();
+    const uint64_t slot = (uint64_t)tile * G::TW;
+    for (uint32_t i = t; i < total; i += FNT) {
+      a.stg_hash[slot + i] = sh_hash[i];
+      a.stg_pos[slot + i] = sh_pos[i];
+      if (BAR == BAR_READS) a.stg_first[slot + i] = sh_first[i];
+    }
+    if (t == 0) a.tile_counts[tile] = total;
+    __syncthreads();
+  }
+}
+
+// Step 3: one warp per tile copies its staged picks to their place (offsets = scanned counts).
+template <int BAR>
+__global__ void k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
+  const uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (tile >= num_tiles) return;
+  const uint32_t o = a.tile_counts[tile], c = a.tile_counts[tile + 1] - o;
+  const uint64_t slot = tile * (uint64_t)TW;
+  uint32_t *gh = static_cast<uint32_t *>(a.hash_out);
+  for (uint32_t i = lane; i < c; i += 32) {
+    const uint64_t gi = (uint64_t)o + i;
+    if (gi < a.capacity) {
+      gh[gi] = a.stg_hash[slot + i];
+      a.pos_out[gi] = a.stg_pos[slot + i];
+    }
+    if (BAR == BAR_READS) {
+      const uint32_t rd = a.stg_first[slot + i];
+      if (rd != 0xFFFFFFFFu) a.pick_offsets[rd] = gi;
+    }
+  }
+  if (tile == num_tiles - 1 && lane == 0) *a.count_out = a.tile_counts[num_tiles];
+}
+
+template <int W, int BAR, int SRC>
+cudaError_t launch_w(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, uint64_t nwin, int span,
+                     int num_sms, cudaStream_t st) {
+  auto kern = k_mini_stage<W, BAR, SRC>;
+  const size_t sm = Geo<W, SRC, BAR>::BYTES;
+  static int per_sm = 0;  // resident CTAs per SM for this instantiation
+  if (per_sm == 0) {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, FNT, sm);
+    if (e != cudaSuccess) return e;
+    per_sm = b > 0 ? b : 1;
+  }
+  uint64_t grid = (uint64_t)per_sm * (uint64_t)num_sms;
+  if (grid > num_tiles) grid = num_tiles;
+  kern<<<(unsigned)grid, FNT, sm, st>>>(a, nwin, span, tile_bar, (uint32_t)num_tiles);
+  return cudaGetLastError();
+}
+
+template <int BAR, int SRC>
+cudaError_t launch_bar(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, uint64_t nwin, int span,
+                       int num_sms, cudaStream_t st) {
+  switch (a.w) {
+    case 4: return launch_w<4, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 5: return launch_w<5, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 6: return launch_w<6, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 7: return launch_w<7, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 8: return launch_w<8, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 9: return launch_w<9, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 10: return launch_w<10, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 11: return launch_w<11, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 12: return launch_w<12, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 13: return launch_w<13, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 14: return launch_w<14, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 15: return launch_w<15, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 16: return launch_w<16, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace
+
+bool mini_fast_applies(int source, int k, int w) {
+  return w >= 4 && w <= 16 && (source == SRC_KEYS || 2 * k <= 32);
+}
+
+int mini_fast_tile_windows(int w) { return w >= 4 && w <= 16 ? (FNT * (16 / w) - 2) * w : 0; }
+
+cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, cudaStream_t st) {
+  if (num_tiles == 0) return cudaSuccess;
+  if (num_tiles >= 0xffffffffull) return cudaErrorInvalidValue;
+  const int TW = mini_fast_tile_windows(a.w);
+  const int span = source == SRC_DNA ? a.w + a.k - 1 : a.w;
+  const uint64_t nwin = a.n >= (uint64_t)span ? a.n - span + 1 : 0;
+  cudaError_t e = launch_tile_barriers(a, source, barrier, num_tiles, TW, span, st);
+  if (e != cudaSuccess) return e;
+  const uint2 *tile_bar = tile_barriers_needed(a, source, barrier) ? a.tile_bar : nullptr;
+  int dev = 0, num_sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (source == SRC_KEYS) e = launch_bar<BAR_NBLOCK, SRC_KEYS>(a, num_tiles, nullptr, nwin, span, num_sms, st);
+  else if (barrier == BAR_READS) e = launch_bar<BAR_READS, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+  else e = launch_bar<BAR_NBLOCK, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+  if (e != cudaSuccess) return e;
+  e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  const uint64_t blocks = (num_tiles * 32 + 255) / 256;
+  if (barrier == BAR_READS) k_mini_gather<BAR_READS><<<(unsigned)blocks, 256, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  else k_mini_gather<BAR_NBLOCK><<<(unsigned)blocks, 256, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  return cudaGetLastError();
+}
+
+}  // namespace sws

@@ -5,9 +5,9 @@
 // Some callers cannot allocate: code running inside a device-memory allocator's own hooks (an
 // allocation there would re-enter the allocator), programs whose device memory is fully handed
 // out in advance by a framework that owns every byte, and latency-critical paths that must not
-// pay for, or risk the failure of, an allocation.  For them, sws_minimizers_noalloc runs the same
-// kernel with its scratch in a fixed array that this file declares in device global memory; a
-// call allocates nothing and needs no context.
+// pay for, or risk the failure of, an allocation.  For them, sws_minimizers_noalloc runs the
+// single-kernel (look-back) minimizer path with its scratch in a fixed array that this file
+// declares in device global memory; a call allocates nothing and needs no context.
 //
 // The array lives as long as the library is loaded, on every device that loads it (4 MiB each).
 // Its device address is looked up once per device (cudaGetSymbolAddress, with that device
@@ -67,7 +67,7 @@ extern "C" sws_status sws_minimizers_noalloc(const uint8_t *seq, uint64_t n, int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t span = (uint64_t)(w + k - 1);
   const uint64_t nwin = n >= span ? n - span + 1 : 0;
-  const uint64_t tiles = sws::mini_num_tiles(nwin, w);
+  const uint64_t tiles = sws::mini_lookback_tiles(nwin, w);
   if (tiles == 0) {
     cudaError_t e = cudaMemsetAsync(count_out, 0, sizeof(uint64_t), st);
     return e == cudaSuccess ? SWS_OK : sws::report_error(SWS_ERR_CUDA, cudaGetErrorString(e));
@@ -107,7 +107,7 @@ extern "C" sws_status sws_minimizers_noalloc(const uint8_t *seq, uint64_t n, int
   a.tile_counter = reinterpret_cast<unsigned int *>(base + 128);
   a.status = reinterpret_cast<unsigned long long *>(base + kNoallocHeader);
   a.tile_bar = reinterpret_cast<uint2 *>(base + kNoallocHeader + kNoallocMaxTiles * 8);
-  e = sws::launch_minimizers(a, sws::SRC_DNA, sws::BAR_NBLOCK, tiles, st);
+  e = sws::launch_minimizers_lookback(a, sws::SRC_DNA, sws::BAR_NBLOCK, tiles, st);
   if (e != cudaSuccess) return sws::report_error(SWS_ERR_CUDA, cudaGetErrorString(e));
   return SWS_OK;
 }

@@ -311,15 +311,6 @@ __global__ void k_offsets_gaps(uint64_t *__restrict__ offsets, const Gap *__rest
   }
 }
 
-cudaError_t scan_u32(uint32_t *a, uint64_t len, uint32_t *bsum, cudaStream_t st) {
-  const uint64_t nb = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
-  if (nb == 0) return cudaSuccess;
-  k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
-  k_scan_blocks<<<1, SCAN_NT, 0, st>>>(bsum, nb);
-  k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
-  return cudaGetLastError();
-}
-
 template <bool WIDE>
 cudaError_t sort_t(const TableArgs &a, cudaStream_t st) {
   const uint64_t m = a.m;
@@ -377,6 +368,17 @@ cudaError_t offsets_t(const TableArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+uint64_t scan_u32_scratch_words(uint64_t len) { return (len + SCAN_BLOCK - 1) / SCAN_BLOCK + 1; }
+
+cudaError_t scan_u32(uint32_t *a, uint64_t len, uint32_t *bsum, cudaStream_t st) {
+  const uint64_t nb = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  if (nb == 0) return cudaSuccess;
+  k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
+  k_scan_blocks<<<1, SCAN_NT, 0, st>>>(bsum, nb);
+  k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
+  return cudaGetLastError();
+}
 
 uint64_t table_gap_capacity(int bucket_bits) { return ((1ull << bucket_bits) + 1) / (GAP_DIRECT + 1) + 2; }
 uint64_t table_hist_words(uint64_t m) { return (uint64_t)RBINS * ((m + RTILE - 1) / RTILE); }

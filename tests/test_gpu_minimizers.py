@@ -127,3 +127,28 @@ def test_minimizers_batch_matches_per_read_oracle():
         rh, rp, rpo = oracle.minimizers_batch(seq, offs, k, w, mode)
         assert (po.cpu().numpy().view(np.uint64) == rpo).all()
         assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+
+
+# Every window length of the kernel specialized on w (4..16, keys of at most 32 bits), at sizes
+# that span several of its tiles ((256 * floor(16/w) - 2) * w windows each) with a ragged tail.
+@pytest.mark.parametrize("w", list(range(4, 17)))
+def test_specialized_window_lengths(w):
+    rng = np.random.default_rng(1000 + w)
+    tw = (256 * (16 // w) - 2) * w
+    for k, mode in ((15, "hash"), (16, "fwd"), (5, "canonical")):
+        n = 3 * tw + int(rng.integers(1, tw))
+        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+        check_minimizers(seq, n, k, w, mode)
+        iv = random_nblocks(n, rng, 6, 3 * w)
+        check_minimizers(seq, n, k, w, mode, iv)
+    keys = rng.integers(0, 1000, size=2 * tw + 17, dtype=np.int64).astype(np.uint32)
+    h, p = B.minimizers_from_keys(torch.from_numpy(keys.view(np.int32)).cuda(), w)
+    rh, rp = oracle.minimizers_from_keys(keys.astype(np.uint64), w)
+    assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+    lens = rng.integers(0, 3 * w + 40, size=300)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    bseq = synth.acgt_uniform_packed(int(offs[-1]), seed=w)
+    bh, bp, bpo = B.minimizers_batch(bseq.cuda(), torch.from_numpy(offs).cuda(), int(offs[-1]), 15, w)
+    rh, rp, rpo = oracle.minimizers_batch(bseq, offs, 15, w)
+    assert (bpo.cpu().numpy().view(np.uint64) == rpo).all()
+    assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
