@@ -139,6 +139,44 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
                                 uint64_t total_bases, int k, int w, int mode, void *hash_out, uint32_t *pos_out,
                                 uint64_t capacity, uint64_t *pick_offsets, uint64_t *count_out, void *stream);
 
+/* ---- batched minimizers in one captured graph (Sec. 2.4 per read) ------------------------- */
+/* A reusable pipeline for batches of up to max_reads reads and max_bases bases with fixed k, w
+ * and key mode.  All buffers are allocated at creation; sws_batch_run replays one captured CUDA
+ * graph (one persistent minimizer launch plus its scan, gather and fix-up kernels) whatever the
+ * size of the batch, reading the sizes from a device descriptor.  Results are those of
+ * sws_minimizers_batch on the same reads.
+ *   options: SWS_BATCH_DEFAULT picks the kernel specialized on w when it applies (4 <= w <= 16,
+ *            k <= 16), SWS_BATCH_TUNE times it against the single-kernel look-back path on a
+ *            synthetic batch of the largest size and keeps the faster (see sws_batch_io.tuned_ms),
+ *            SWS_BATCH_LOOKBACK forces the look-back path.
+ * One run may be in flight per object: sws_batch_run waits for the previous run to finish before
+ * it overwrites the descriptor.  Use one object per concurrent stream. */
+typedef struct sws_batch sws_batch;
+#define SWS_BATCH_DEFAULT 0
+#define SWS_BATCH_TUNE 1
+#define SWS_BATCH_LOOKBACK 2
+typedef struct sws_batch_io {
+  uint8_t *seq;            /* device input: packed bases of the reads back to back, >= max_bases */
+  int64_t *offsets;        /* device input: read r = bases [offsets[r], offsets[r+1]), max_reads+1 */
+  void *hash;              /* device output: pick keys (uint32 when 2k <= 32, else uint64)      */
+  uint32_t *pos;           /* device output: read-local pick positions                          */
+  uint64_t *pick_offsets;  /* device output: [max_reads+1], as in sws_minimizers_batch          */
+  uint64_t *count;         /* device output: number of picks                                    */
+  uint64_t capacity;       /* entries of hash/pos (= max_bases, never exceeded)                  */
+  uint64_t max_reads, max_bases;
+  int path;                /* 0: kernel specialized on w, 1: look-back kernel                    */
+  float tuned_ms[2];       /* measured ms per largest batch for each path (-1: not timed)        */
+} sws_batch_io;
+sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases, int k, int w, int mode,
+                            int options, sws_batch **out);
+sws_status sws_batch_destroy(sws_batch *b);
+/* The batch's device buffers (owned by the batch; valid until sws_batch_destroy). */
+sws_status sws_batch_io_get(sws_batch *b, sws_batch_io *io);
+/* Process the first nreads reads (total_bases bases) already in io.seq / io.offsets, on stream. */
+sws_status sws_batch_run(sws_batch *b, uint64_t nreads, uint64_t total_bases, void *stream);
+/* Wait for the last run and report a device-side fault (SWS_ERR_TIMEOUT) if one occurred. */
+sws_status sws_batch_sync(sws_batch *b);
+
 /* ---- minimizers without allocation ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that cannot allocate
  * device memory: code running inside a device-memory allocator's hooks (allocating there would

@@ -53,7 +53,18 @@ SIGNATURES = {
     "sws_minimizers_batch": (i32, [vp, vp, vp, u64, u64, i32, i32, i32, vp, vp, u64, vp, vp, vp]),
     "sws_kmer_table": (i32, [vp, vp, vp, u64, i32, i32, vp, vp, vp, vp]),
     "sws_minimizers_noalloc": (i32, [vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
+    "sws_batch_create": (i32, [vp, u64, u64, i32, i32, i32, i32, ctypes.POINTER(vp)]),
+    "sws_batch_destroy": (i32, [vp]),
+    "sws_batch_io_get": (i32, [vp, vp]),
+    "sws_batch_run": (i32, [vp, u64, u64, vp]),
+    "sws_batch_sync": (i32, [vp]),
 }
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [("seq", vp), ("offsets", vp), ("hash", vp), ("pos", vp), ("pick_offsets", vp), ("count", vp),
+                ("capacity", u64), ("max_reads", u64), ("max_bases", u64), ("path", i32),
+                ("tuned_ms", ctypes.c_float * 2)]
 
 
 def library_path() -> str:
@@ -267,3 +278,69 @@ def kmer_table(hashes: torch.Tensor, pos: torch.Tensor, hash_bits: int, bucket_b
     _check(load().sws_kmer_table(ctx.handle, _ptr(hashes), _ptr(pos), m, int(hash_bits), int(bucket_bits), _ptr(sh),
                                  _ptr(sp), _ptr(off), _stream(stream)))
     return sh, sp, off
+
+
+class _DevArray:
+    """A view of library-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+BATCH_OPTIONS = {"default": 0, "tune": 1, "lookback": 2}
+
+
+class Batch:
+    """A reusable batched-minimizer pipeline replayed as one CUDA graph (sws_batch_*)."""
+
+    def __init__(self, max_reads: int, max_bases: int, k: int, w: int, mode: str = "hash", options: str = "default",
+                 ctx: Context | None = None):
+        self.ctx = ctx or default_context()
+        h = vp()
+        _check(load().sws_batch_create(self.ctx.handle, int(max_reads), int(max_bases), int(k), int(w),
+                                       MINI_MODES[mode], BATCH_OPTIONS[options], ctypes.byref(h)))
+        self.handle = h
+        io = BatchIO()
+        _check(load().sws_batch_io_get(self.handle, ctypes.byref(io)))
+        self.io = io
+        self.k = k
+        dev = torch.device("cuda", self.ctx.device)
+        hs = "<u4" if 2 * k <= 32 else "<u8"
+        self.seq = torch.as_tensor(_DevArray(io.seq, ((int(max_bases) + 3) // 4,), "|u1"), device=dev)
+        self.offsets = torch.as_tensor(_DevArray(io.offsets, (int(max_reads) + 1,), "<i8"), device=dev)
+        self.hash = torch.as_tensor(_DevArray(io.hash, (int(io.capacity),), hs.replace("u", "i")), device=dev)
+        self.pos = torch.as_tensor(_DevArray(io.pos, (int(io.capacity),), "<i4"), device=dev)
+        self.pick_offsets = torch.as_tensor(_DevArray(io.pick_offsets, (int(max_reads) + 1,), "<i8"), device=dev)
+        self.count = torch.as_tensor(_DevArray(io.count, (1,), "<i8"), device=dev)
+        self.path = int(io.path)
+        self.tuned_ms = (float(io.tuned_ms[0]), float(io.tuned_ms[1]))
+        self.nreads = 0
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.sws_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, seq: torch.Tensor, offsets: torch.Tensor, stream=None):
+        """Copy packed reads and their offsets (device or host tensors) into the batch buffers."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            self.seq[: seq.numel()].copy_(seq, non_blocking=True)
+            self.offsets[: offsets.numel()].copy_(offsets, non_blocking=True)
+
+    def run(self, nreads: int, total_bases: int, stream=None):
+        _check(load().sws_batch_run(self.handle, int(nreads), int(total_bases), _stream(stream)))
+        self.nreads = int(nreads)
+
+    def results(self):
+        """(keys, positions, pick offsets) of the last run (waits for it)."""
+        _check(load().sws_batch_sync(self.handle))
+        c = int(self.count.item())
+        return self.hash[:c], self.pos[:c], self.pick_offsets[: self.nreads + 1]

@@ -9,14 +9,6 @@
 #include "../../include/sws.h"
 #include "internal.h"
 
-struct sws_ctx {
-  int device = 0;
-  int *d_err = nullptr;      // device error word (DevErr bits)
-  void *ws = nullptr;        // workspace
-  uint64_t ws_size = 0;
-  int num_sms = 0;
-};
-
 namespace {
 
 thread_local std::string g_err = "no error";

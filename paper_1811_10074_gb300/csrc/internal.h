@@ -4,6 +4,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// The context behind the opaque sws_ctx handle of the C ABI.
+struct sws_ctx {
+  int device = 0;
+  int *d_err = nullptr;  // device error word (DevErr bits)
+  void *ws = nullptr;    // workspace
+  uint64_t ws_size = 0;
+  int num_sms = 0;
+};
+
 namespace sws {
 
 // Tile configurations of the sliding-sum kernels: threads per CTA x elements per thread.
@@ -48,7 +57,14 @@ struct MiniArgs {
   uint32_t *stg_hash;     // [num_tiles * windows per tile]
   uint32_t *stg_pos;
   uint32_t *stg_first;    // read batches: read index of a read's first pick, else ~0
+  // When set, the sizes (n, nbar, windows, tiles) are read from this device descriptor at run
+  // time instead of from the fields above: one captured graph then serves any batch up to the
+  // sizes it was built for.  Layout: see BatchDesc.
+  const unsigned long long *desc;
 };
+
+// Device descriptor of a batch, read by the kernels of a captured batch graph.
+enum BatchDesc { BD_NREADS = 0, BD_TOTAL = 1, BD_NWIN = 2, BD_TILES = 3, BD_SCAN_LEN = 4, BD_WORDS = 8 };
 
 enum MiniSource { SRC_DNA = 0, SRC_KEYS = 1 };
 enum MiniBarrier { BAR_NBLOCK = 0, BAR_READS = 1 };
@@ -65,6 +81,7 @@ bool mini_fast_applies(int source, int k, int w);
 int mini_fast_tile_windows(int w);
 cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
                                      cudaStream_t stream);
+
 // The per-tile summary of the barriers (N-blocks or read starts) that can touch each tile.
 bool tile_barriers_needed(const MiniArgs &a, int source, int barrier);
 cudaError_t launch_tile_barriers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, int TW, int span,
@@ -72,9 +89,14 @@ cudaError_t launch_tile_barriers(const MiniArgs &a, int source, int barrier, uin
 // Exclusive scan of uint32 counts in place (scratch of scan_u32_scratch_words(len) words).
 uint64_t scan_u32_scratch_words(uint64_t len);
 cudaError_t scan_u32(uint32_t *a, uint64_t len, uint32_t *bsum, cudaStream_t stream);
-// Batch fix-up: reads without picks get the offset of the next read that has some.
+// The same with the length read at run time from *dlen (at most max_len).
+cudaError_t scan_u32_dev(uint32_t *a, uint64_t max_len, const unsigned long long *dlen, uint32_t *bsum,
+                         cudaStream_t stream);
+// Batch fix-up: reads without picks get the offset of the next read that has some.  With `desc`
+// set, the number of reads is read from it at run time (nreads is then the maximum).
 cudaError_t launch_pick_offsets_fixup(uint64_t *pick_offsets, uint64_t nreads, const uint64_t *count,
-                                      uint64_t *scratch, cudaStream_t stream);
+                                      uint64_t *scratch, cudaStream_t stream,
+                                      const unsigned long long *desc = nullptr);
 // k-mer values.
 cudaError_t launch_kmers(const uint8_t *seq, uint64_t n, int k, int kind, void *out, int *err, cudaStream_t stream);
 

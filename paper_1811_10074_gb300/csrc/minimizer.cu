@@ -68,6 +68,12 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
+  uint64_t n = a.n;  // bases (or keys)
+  if (a.desc) {  // a batch graph launched for the largest batch: sizes of this run
+    n = a.desc[BD_TOTAL];
+    nwin = a.desc[BD_NWIN];
+    if (tile >= a.desc[BD_TILES]) return;
+  }
   const long long p0 = (long long)tile * TW;  // first emitted window of the tile
   const long long ifirst = p0 - 1;             // k-mer / window of local index 0
 
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   bool ok = true;
   if (SRC == SRC_DNA) {
     if (t == 0) s_phase = (int)((unsigned long long)(ifirst + a.w) % (unsigned long long)a.w);
-    ok = stage_bytes(sbases, a.seq, (a.n + 3) / 4, p0 / 4 - 16, STAGE_BYTES_MINI, &s_mbar, a.err);
+    ok = stage_bytes(sbases, a.seq, (n + 3) / 4, p0 / 4 - 16, STAGE_BYTES_MINI, &s_mbar, a.err);
     const uint32_t *W = reinterpret_cast<const uint32_t *>(sbases);
     const int k = a.k;
     if (2 * k <= 32) {
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
         const long long i = ifirst + t * MVPT + j;
         const Kmer32 q = kmer32(bits, k, kmask);
         const uint32_t v = key_value32(q, a.mode, kmask);
-        x[j] = (i >= 0 && (unsigned long long)i + k <= a.n) ? KT::make(v, (uint32_t)i) : KT::none();
+        x[j] = (i >= 0 && (unsigned long long)i + k <= n) ? KT::make(v, (uint32_t)i) : KT::none();
       }
     } else {
       const unsigned long long kmask = 0xFFFFFFFFFFFFFFFFull >> (64 - 2 * k);
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
         const long long i = ifirst + t * MVPT + j;
         const Kmer64 q = kmer64(bits, k, kmask);
         const unsigned long long v = key_value64(q, a.mode, kmask);
-        x[j] = (i >= 0 && (unsigned long long)i + k <= a.n) ? KT::make(v, (uint32_t)i) : KT::none();
+        x[j] = (i >= 0 && (unsigned long long)i + k <= n) ? KT::make(v, (uint32_t)i) : KT::none();
       }
     }
   } else {
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
 #pragma unroll
     for (int j = 0; j < MVPT; ++j) {
       const long long i = ifirst + t * MVPT + j;
-      x[j] = (i >= 0 && (unsigned long long)i < a.n) ? KT::make(__ldg(a.keys + i), (uint32_t)i) : KT::none();
+      x[j] = (i >= 0 && (unsigned long long)i < n) ? KT::make(__ldg(a.keys + i), (uint32_t)i) : KT::none();
     }
     __syncthreads();
   }
@@ -272,7 +278,11 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
 // Per tile: the first barrier that can touch its windows and how many can.
 template <int BAR>
 __global__ void k_tile_barriers(const int64_t *__restrict__ bar, uint64_t nbar, uint64_t ntiles, int TW, int span,
-                                uint2 *__restrict__ out) {
+                                uint2 *__restrict__ out, const unsigned long long *__restrict__ desc) {
+  if (desc) {
+    nbar = desc[BD_NREADS];
+    ntiles = desc[BD_TILES];
+  }
   const uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tile >= ntiles) return;
   const long long lo_lim = (long long)tile * TW - 1;            // first window of the tile
@@ -352,8 +362,10 @@ __global__ void __launch_bounds__(MNT) k_kmers(const uint8_t *__restrict__ seq, 
 // ---- batch pick offsets: suffix minimum ------------------------------------------------------
 constexpr int FIX_NT = 256, FIX_PER = 4, FIX_BLOCK = FIX_NT * FIX_PER;
 
-__global__ void k_fix_block_min(const uint64_t *__restrict__ po, uint64_t nreads, uint64_t *__restrict__ bmin) {
+__global__ void k_fix_block_min(const uint64_t *__restrict__ po, uint64_t nreads, uint64_t *__restrict__ bmin,
+                                const unsigned long long *__restrict__ desc) {
   __shared__ uint64_t s[FIX_NT];
+  if (desc) nreads = desc[BD_NREADS];
   const uint64_t b0 = (uint64_t)blockIdx.x * FIX_BLOCK;
   uint64_t v = ~0ull;
   for (int j = 0; j < FIX_PER; ++j) {
@@ -370,8 +382,10 @@ __global__ void k_fix_block_min(const uint64_t *__restrict__ po, uint64_t nreads
 }
 
 // Exclusive suffix minimum over the block minima, seeded with the total count.
-__global__ void k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks, const uint64_t *__restrict__ count) {
+__global__ void k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks, const uint64_t *__restrict__ count,
+                           const unsigned long long *__restrict__ desc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (desc) nblocks = (desc[BD_NREADS] + FIX_BLOCK - 1) / FIX_BLOCK;
   uint64_t carry = *count;
   for (uint64_t b = nblocks; b-- > 0;) {
     const uint64_t v = bmin[b];
@@ -381,8 +395,11 @@ __global__ void k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks, const 
 }
 
 __global__ void k_fix_apply(uint64_t *__restrict__ po, uint64_t nreads, const uint64_t *__restrict__ bcarry,
-                            const uint64_t *__restrict__ count) {
+                            const uint64_t *__restrict__ count, const unsigned long long *__restrict__ desc) {
   __shared__ uint64_t s[FIX_BLOCK];
+  if (desc) nreads = desc[BD_NREADS];
+  if ((uint64_t)blockIdx.x * FIX_BLOCK >= nreads && blockIdx.x > 0) return;
+  const uint64_t *carry_src = nreads == 0 ? count : bcarry;
   const uint64_t b0 = (uint64_t)blockIdx.x * FIX_BLOCK;
   for (int j = threadIdx.x; j < FIX_BLOCK; j += FIX_NT) {
     const uint64_t i = b0 + j;
@@ -390,7 +407,7 @@ __global__ void k_fix_apply(uint64_t *__restrict__ po, uint64_t nreads, const ui
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint64_t carry = bcarry[blockIdx.x];
+    uint64_t carry = nreads == 0 ? *count : carry_src[blockIdx.x];
     for (int j = FIX_BLOCK - 1; j >= 0; --j) {
       carry = min(carry, s[j]);
       s[j] = carry;
@@ -428,6 +445,7 @@ int mini_tile_windows(int w) {
 }
 
 bool tile_barriers_needed(const MiniArgs &a, int source, int barrier) {
+  if (a.desc) return source == SRC_DNA && barrier == BAR_READS;  // batch graphs: decided at run time
   return source == SRC_DNA && ((barrier == BAR_NBLOCK && a.nbar > 0) || (barrier == BAR_READS && a.nbar > 1));
 }
 
@@ -436,9 +454,9 @@ cudaError_t launch_tile_barriers(const MiniArgs &a, int source, int barrier, uin
   if (!tile_barriers_needed(a, source, barrier) || num_tiles == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((num_tiles + 255) / 256);
   if (barrier == BAR_NBLOCK)
-    k_tile_barriers<BAR_NBLOCK><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, a.tile_bar);
+    k_tile_barriers<BAR_NBLOCK><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, a.tile_bar, a.desc);
   else
-    k_tile_barriers<BAR_READS><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, a.tile_bar);
+    k_tile_barriers<BAR_READS><<<blocks, 256, 0, st>>>(a.bar, a.nbar, num_tiles, TW, span, a.tile_bar, a.desc);
   return cudaGetLastError();
 }
 
@@ -469,15 +487,15 @@ cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrie
 }
 
 cudaError_t launch_pick_offsets_fixup(uint64_t *po, uint64_t nreads, const uint64_t *count, uint64_t *scratch,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, const unsigned long long *desc) {
   const uint64_t nblocks = (nreads + FIX_BLOCK - 1) / FIX_BLOCK;
   if (nblocks == 0) {
-    k_fix_apply<<<1, FIX_NT, 0, st>>>(po, 0, count, count);
+    k_fix_apply<<<1, FIX_NT, 0, st>>>(po, 0, count, count, desc);
     return cudaGetLastError();
   }
-  k_fix_block_min<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch);
-  k_fix_scan<<<1, 32, 0, st>>>(scratch, nblocks, count);
-  k_fix_apply<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, count);
+  k_fix_block_min<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, desc);
+  k_fix_scan<<<1, 32, 0, st>>>(scratch, nblocks, count, desc);
+  k_fix_apply<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, count, desc);
   return cudaGetLastError();
 }
 

@@ -84,8 +84,14 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
   __shared__ uint32_t s_wcount[FNW];
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint64_t n = a.n;
+  if (a.desc) {  // a batch graph: sizes of this run
+    n = a.desc[BD_TOTAL];
+    nwin = a.desc[BD_NWIN];
+    num_tiles = (uint32_t)a.desc[BD_TILES];
+  }
   const uint8_t *src = SRC == SRC_DNA ? a.seq : reinterpret_cast<const uint8_t *>(a.keys);
-  const uint64_t nbytes = SRC == SRC_DNA ? (a.n + 3) / 4 : a.n * 4;
+  const uint64_t nbytes = SRC == SRC_DNA ? (n + 3) / 4 : n * 4;
   const bool src_aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
 
   // Thread 0: start the bulk copy of tile `tile`'s bases (or keys) into buffer b.
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     const long long ifirst = i0 + (long long)t * VPT;
     const long long tlo = p0 - 1, thi = p0 + G::TW - 1;  // windows this tile looks at
     const bool interior = nb == 0 && tlo >= 0 && (unsigned long long)thi < nwin;
-    const long long lastv = (long long)a.n - (SRC == SRC_DNA ? a.k : 1);  // last valid k-mer
+    const long long lastv = (long long)n - (SRC == SRC_DNA ? a.k : 1);  // last valid k-mer
     const int jlo = interior ? 0 : (ifirst < 0 ? (int)(-ifirst < VPT ? -ifirst : VPT) : 0);
     const int jhi = interior ? VPT : (lastv < ifirst ? 0 : (int)(lastv - ifirst + 1 < VPT ? lastv - ifirst + 1 : VPT));
     uint32_t x[VPT];
@@ -366,8 +372,10 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 // Step 3: one warp per tile copies its staged picks to their place (offsets = scanned counts).
 template <int BAR>
 __global__ void k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
+  if (a.desc) num_tiles = (uint32_t)a.desc[BD_TILES];
   const uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = a.tile_counts[num_tiles];
   if (tile >= num_tiles) return;
   const uint32_t o = a.tile_counts[tile], c = a.tile_counts[tile + 1] - o;
   const uint64_t slot = tile * (uint64_t)TW;
@@ -383,7 +391,6 @@ __global__ void k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
       if (rd != 0xFFFFFFFFu) a.pick_offsets[rd] = gi;
     }
   }
-  if (tile == num_tiles - 1 && lane == 0) *a.count_out = a.tile_counts[num_tiles];
 }
 
 template <int W, int BAR, int SRC>
@@ -454,7 +461,8 @@ cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier,
   else if (barrier == BAR_READS) e = launch_bar<BAR_READS, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
   else e = launch_bar<BAR_NBLOCK, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
   if (e != cudaSuccess) return e;
-  e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
+  if (a.desc) e = scan_u32_dev(a.tile_counts, num_tiles + 1, a.desc + BD_SCAN_LEN, a.scan_tmp, st);
+  else e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
   const uint64_t blocks = (num_tiles * 32 + 255) / 256;
   if (barrier == BAR_READS) k_mini_gather<BAR_READS><<<(unsigned)blocks, 256, 0, st>>>(a, (uint32_t)num_tiles, TW);

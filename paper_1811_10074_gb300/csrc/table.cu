@@ -103,9 +103,12 @@ __global__ void __launch_bounds__(RNT) k_radix_hist(PassIn in, uint64_t m, int s
 
 // ---- exclusive scan of uint32 counts (three kernels) ------------------------------------------
 __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const uint32_t *__restrict__ a, uint64_t len,
-                                                         uint32_t *__restrict__ bsum) {
+                                                         uint32_t *__restrict__ bsum,
+                                                         const unsigned long long *__restrict__ dlen) {
   __shared__ uint32_t s[SCAN_NT / 32];
+  if (dlen) len = *dlen;
   const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_BLOCK;
+  if (b0 >= len && b0 > 0) return;
   uint32_t v = 0;
   for (int j = 0; j < SCAN_PER; ++j) {
     const uint64_t i = b0 + (uint64_t)j * SCAN_NT + threadIdx.x;
@@ -122,9 +125,11 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const uint32_t *__restr
 }
 
 // Exclusive scan of the block sums by one CTA (sequential over chunks of SCAN_NT).
-__global__ void __launch_bounds__(SCAN_NT) k_scan_blocks(uint32_t *__restrict__ bsum, uint64_t nb) {
+__global__ void __launch_bounds__(SCAN_NT) k_scan_blocks(uint32_t *__restrict__ bsum, uint64_t nb,
+                                                         const unsigned long long *__restrict__ dlen) {
   __shared__ uint32_t s[SCAN_NT / 32];
   __shared__ uint32_t carry;
+  if (dlen) nb = (*dlen + SCAN_BLOCK - 1) / SCAN_BLOCK;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
@@ -152,8 +157,11 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_blocks(uint32_t *__restrict__ 
 }
 
 __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(uint32_t *__restrict__ a, uint64_t len,
-                                                        const uint32_t *__restrict__ bsum) {
+                                                        const uint32_t *__restrict__ bsum,
+                                                        const unsigned long long *__restrict__ dlen) {
   __shared__ uint32_t s[SCAN_NT / 32];
+  if (dlen) len = *dlen;
+  if ((uint64_t)blockIdx.x * SCAN_BLOCK >= len) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_BLOCK + (uint64_t)threadIdx.x * SCAN_PER;
   uint32_t v[SCAN_PER];
@@ -374,9 +382,19 @@ uint64_t scan_u32_scratch_words(uint64_t len) { return (len + SCAN_BLOCK - 1) / 
 cudaError_t scan_u32(uint32_t *a, uint64_t len, uint32_t *bsum, cudaStream_t st) {
   const uint64_t nb = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
   if (nb == 0) return cudaSuccess;
-  k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
-  k_scan_blocks<<<1, SCAN_NT, 0, st>>>(bsum, nb);
-  k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum);
+  k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum, nullptr);
+  k_scan_blocks<<<1, SCAN_NT, 0, st>>>(bsum, nb, nullptr);
+  k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, len, bsum, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t scan_u32_dev(uint32_t *a, uint64_t max_len, const unsigned long long *dlen, uint32_t *bsum,
+                         cudaStream_t st) {
+  const uint64_t nb = (max_len + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  if (nb == 0) return cudaSuccess;
+  k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, max_len, bsum, dlen);
+  k_scan_blocks<<<1, SCAN_NT, 0, st>>>(bsum, nb, dlen);
+  k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(a, max_len, bsum, dlen);
   return cudaGetLastError();
 }
 

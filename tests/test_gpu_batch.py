@@ -1,0 +1,76 @@
+"""Batched minimizers replayed as one CUDA graph (sws_batch_*) against the per-read oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_10074_gb300 import binding as B
+from paper_1811_10074_gb300 import synth
+from gpu_common import require_gpu, to_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def make_batch(rng, nreads, lo, hi, seed):
+    lens = rng.integers(lo, hi + 1, size=nreads)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    seq = synth.acgt_uniform_packed(int(offs[-1]), seed=seed)
+    return seq, offs
+
+
+def check_run(bt, seq, offs, k, w, mode="hash"):
+    nreads = offs.size - 1
+    total = int(offs[-1])
+    bt.load(seq.cuda(), torch.from_numpy(offs).cuda())
+    bt.run(nreads, total)
+    h, p, po = bt.results()
+    rh, rp, rpo = oracle.minimizers_batch(seq, offs, k, w, mode)
+    assert (po.cpu().numpy().view(np.uint64) == rpo).all()
+    assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+    return h.numel()
+
+
+@pytest.mark.parametrize("options", ["default", "lookback", "tune"])
+def test_batch_graph_replays_any_size(options):
+    rng = np.random.default_rng({"default": 1, "lookback": 2, "tune": 3}[options])
+    bt = B.Batch(max_reads=3000, max_bases=600_000, k=15, w=10, options=options)
+    if options == "tune":
+        assert all(t > 0 for t in bt.tuned_ms) and bt.path in (0, 1)
+    assert bt.path == {"default": 0, "lookback": 1}.get(options, bt.path)
+    batches = [make_batch(rng, 2000, 100, 250, 11), make_batch(rng, 30, 1000, 20000, 12),
+               make_batch(rng, 3000, 0, 30, 13), make_batch(rng, 1, 50, 50, 14), make_batch(rng, 2999, 150, 199, 15)]
+    for seq, offs in batches:
+        check_run(bt, seq, offs, 15, 10)
+    # an empty batch
+    bt.run(0, 0)
+    h, p, po = bt.results()
+    assert h.numel() == 0 and int(po[0]) == 0
+    # the same batch again, after others: identical output
+    seq, offs = batches[0]
+    assert check_run(bt, seq, offs, 15, 10) > 0
+    bt.close()
+
+
+def test_batch_wide_keys_use_lookback():
+    rng = np.random.default_rng(5)
+    bt = B.Batch(max_reads=500, max_bases=200_000, k=19, w=10)
+    assert bt.path == 1
+    for i in range(2):
+        seq, offs = make_batch(rng, 400, 60, 400, 20 + i)
+        check_run(bt, seq, offs, 19, 10)
+    bt.close()
+
+
+def test_batch_rejects_oversized_runs():
+    bt = B.Batch(max_reads=10, max_bases=1000, k=15, w=10)
+    with pytest.raises(B.SwsError, match="INVALID"):
+        bt.run(11, 100)
+    with pytest.raises(B.SwsError, match="INVALID"):
+        bt.run(5, 1001)
+    bt.close()
