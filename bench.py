@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
-    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers"],
+    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "batch"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
@@ -283,6 +283,7 @@ def run_ours(args, world, rank, local):
                                             f"{dt:.1f} s single-threaded naive O(wN)"}
     if not args.no_extras and rank == 0:
         result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
+        result["batched_reads"] = batch_extras(dev, ctx)
     del xs, outs
     torch.cuda.empty_cache()
     return result
@@ -387,6 +388,76 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
     return out
 
 
+def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain_sample: int = 20_000, reps: int = 5):
+    """Batched reads: 1e6 short reads U[100,250] + 2e4 log-normal long reads (median 10 kb, max
+    200 kb), k=15 w=10, in one replayed graph (autotuned), against plain per-read launches through
+    the C ABI on a sample of reads with the same length distribution."""
+    import ctypes
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import binding as Bd
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    lens = synth.read_lengths(n_short, n_long)
+    packed, offs = synth.read_batch(lens, device=dev)
+    total, nreads = int(offs[-1]), len(lens)
+    bt = P.Batch(nreads, total, 15, 10, options="tune", ctx=ctx)
+    bt.load(packed, torch.from_numpy(offs).to(dev))
+    bt.run(nreads, total)
+    _, _, _ = bt.results()
+    picks = int(bt.count.item())
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        bt.run(nreads, total, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    bms = a.elapsed_time(b) / reps
+    batched = {"reads": nreads, "bases": total, "picks": picks, "ms": round(bms, 3),
+               "gbp_s": round(total / (bms / 1e3) / 1e9, 1),
+               "path": ["specialized staged", "look-back"][bt.path],
+               "tuned_ms": [round(v, 3) for v in bt.tuned_ms], "graph": True}
+    bt.close()
+    del packed
+    # plain: one sws_minimizers call per read, each read packed from a 16-byte boundary
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(nreads, size=min(plain_sample, nreads), replace=False))
+    slens = lens[idx]
+    poffs = np.zeros(len(slens) + 1, dtype=np.int64)
+    np.cumsum((slens + 63) // 64 * 64, out=poffs[1:])
+    pseq = synth.acgt_uniform_packed(int(poffs[-1]), seed=8, device=dev)
+    cap = int(slens.max())
+    hbuf = torch.empty(cap, dtype=torch.int32, device=dev)
+    pbuf = torch.empty(cap, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    lib = Bd.load()
+    vp = ctypes.c_void_p
+    base = pseq.data_ptr()
+    sh = vp(stream.cuda_stream)
+    args = [(vp(base + int(poffs[i]) // 4), int(slens[i])) for i in range(len(slens))]
+    hp, pp, cp = vp(hbuf.data_ptr()), vp(pbuf.data_ptr()), vp(cnt.data_ptr())
+
+    def plain():
+        for sp, L in args:
+            lib.sws_minimizers(ctx.handle, sp, L, 15, 10, 0, vp(0), 0, hp, pp, cap, cp, sh)
+
+    plain()
+    torch.cuda.synchronize()
+    a.record(stream)
+    t0 = time.perf_counter()
+    plain()
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    pms = a.elapsed_time(b)
+    pbases = int(slens.sum())
+    plain_r = {"reads_timed": len(slens), "bases_timed": pbases, "us_per_read": round(pms * 1e3 / len(slens), 2),
+               "gbp_s": round(pbases / (pms / 1e3) / 1e9, 3), "host_wall_s": round(wall, 3)}
+    return {"workload": "1e6 reads U[100,250] + 2e4 reads ln L ~ N(ln 1e4, 1), L <= 2e5; uniform ACGT; k=15 w=10",
+            "batched_graph": batched, "plain_per_read_launches": plain_r,
+            "speedup_batched_vs_plain": round(batched["gbp_s"] / max(plain_r["gbp_s"], 1e-9), 1)}
+
+
 # ------------------------------------------------------------------------------------------
 # reference arm: the oracle on host cores
 # ------------------------------------------------------------------------------------------
@@ -429,13 +500,17 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section == "minimizers":
+    if args.section in ("minimizers", "batch"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
         dev = torch.device("cuda", torch.cuda.current_device())
+        ctx = P.default_context(dev.index)
         if rank == 0:
-            print(json.dumps({"minimizers": minimizer_extras(dev, P.default_context(dev.index), args.mini_n)}), flush=True)
+            if args.section == "minimizers":
+                print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n)}), flush=True)
+            else:
+                print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
         return
     res = run_ours(args, world, rank, local)
     if rank == 0:

@@ -231,9 +231,11 @@ StagedWs staged_ws_layout(uint64_t tiles, int w, bool reads, uint64_t extra) {
 // applies, look-back path otherwise).  `extra` bytes of workspace are returned in *extra_ptr.
 sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrier, uint64_t nwin, uint64_t extra,
                           void **extra_ptr, cudaStream_t st) {
-  const bool staged = sws::mini_fast_applies(source, a.k, a.w);
+  // The staged path (five launches) pays off once the input fills the GPU; below that the
+  // single-kernel look-back path has the lower latency.
+  const uint64_t tw = (uint64_t)sws::mini_fast_tile_windows(a.w);
+  const bool staged = sws::mini_fast_applies(source, a.k, a.w) && nwin >= 4 * tw * (uint64_t)ctx->num_sms;
   if (staged) {
-    const uint64_t tw = (uint64_t)sws::mini_fast_tile_windows(a.w);
     const uint64_t tiles = (nwin + tw - 1) / tw;
     if (tiles >= 0xffffffffull) return fail(SWS_ERR_INVALID, "input too long");
     const StagedWs L = staged_ws_layout(tiles, a.w, barrier == sws::BAR_READS, extra);

@@ -129,19 +129,22 @@ def test_minimizers_batch_matches_per_read_oracle():
         assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
 
 
-# Every window length of the kernel specialized on w (4..16, keys of at most 32 bits), at sizes
-# that span several of its tiles ((256 * floor(16/w) - 2) * w windows each) with a ragged tail.
+# Every window length of the kernel specialized on w (4..16, keys of at most 32 bits).  The API
+# takes that (staged) path once an input fills the GPU, more than (256 * floor(16/w) - 2) * w
+# windows per SM; 640 tiles plus a ragged tail exceed it on a 152-SM GB300, and a 3-tile input
+# takes the single-kernel look-back path.
 @pytest.mark.parametrize("w", list(range(4, 17)))
 def test_specialized_window_lengths(w):
     rng = np.random.default_rng(1000 + w)
     tw = (256 * (16 // w) - 2) * w
     for k, mode in ((15, "hash"), (16, "fwd"), (5, "canonical")):
-        n = 3 * tw + int(rng.integers(1, tw))
-        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
-        check_minimizers(seq, n, k, w, mode)
-        iv = random_nblocks(n, rng, 6, 3 * w)
-        check_minimizers(seq, n, k, w, mode, iv)
-    keys = rng.integers(0, 1000, size=2 * tw + 17, dtype=np.int64).astype(np.uint32)
+        for ntiles in (640, 3):
+            n = ntiles * tw + int(rng.integers(1, tw))
+            seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+            check_minimizers(seq, n, k, w, mode)
+            iv = random_nblocks(n, rng, 6 + ntiles // 4, 3 * w)
+            check_minimizers(seq, n, k, w, mode, iv)
+    keys = rng.integers(0, 1000, size=640 * tw + 17, dtype=np.int64).astype(np.uint32)
     h, p = B.minimizers_from_keys(torch.from_numpy(keys.view(np.int32)).cuda(), w)
     rh, rp = oracle.minimizers_from_keys(keys.astype(np.uint64), w)
     assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
