@@ -177,6 +177,42 @@ sws_status sws_batch_run(sws_batch *b, uint64_t nreads, uint64_t total_bases, vo
 /* Wait for the last run and report a device-side fault (SWS_ERR_TIMEOUT) if one occurred. */
 sws_status sws_batch_sync(sws_batch *b);
 
+/* ---- serving: a request loop with continuous batching ------------------------------------ */
+/* A server answers minimizer requests (one packed host sequence each; Sec. 2.4 per request)
+ * with continuous batching: a worker thread forms batches from the queued requests in arrival
+ * order and runs each on a free slot (a batch graph, a stream and pinned staging of its own), so
+ * several batches are on the device at once and requests arriving meanwhile join the next batch
+ * as soon as a slot is free.  A request is admitted while the device bytes it needs fit
+ * hbm_budget_bytes next to those in flight.  Results are those of sws_minimizers on the request
+ * alone (uint32 keys, so k <= 16; positions from 0).  Latency is measured from submission to the
+ * moment the worker sees the result on the host. */
+typedef struct sws_server sws_server;
+typedef struct sws_server_config {
+  int k, w, mode;                  /* as for sws_minimizers (k <= 16)                          */
+  uint32_t slots;                  /* batches in flight at once (>= 1)                          */
+  uint64_t max_requests_per_batch; /* requests one batch may hold                               */
+  uint64_t max_bases_per_batch;    /* bases one batch may hold; also the longest request        */
+  uint64_t hbm_budget_bytes;       /* admission budget (0: half the free device memory)         */
+} sws_server_config;
+typedef struct sws_server_statistics {
+  uint64_t completed, batches, bases, pending;
+  double p50_s, p99_s, max_s, mean_s; /* latencies of completed requests                        */
+  double span_s;                      /* first submission to last completion                   */
+} sws_server_statistics;
+sws_status sws_server_create(sws_ctx *ctx, const sws_server_config *cfg, sws_server **out);
+/* Queue a request (the bases are copied; the caller's buffer may be reused at once).
+ * SWS_ERR_CAPACITY if nbases > max_bases_per_batch. */
+sws_status sws_server_submit(sws_server *s, const uint8_t *packed, uint64_t nbases, uint64_t *request_id);
+/* Wait up to timeout_s seconds (0: just look) for a request; *done = 1 once it is answered. */
+sws_status sws_server_wait(sws_server *s, uint64_t request_id, double timeout_s, int *done);
+/* Copy an answered request's picks to host buffers and forget the request. */
+sws_status sws_server_result(sws_server *s, uint64_t request_id, uint32_t *hash, uint32_t *pos, uint64_t capacity,
+                             uint64_t *count, double *latency_s);
+sws_status sws_server_stats(sws_server *s, sws_server_statistics *out);
+sws_status sws_server_reset_stats(sws_server *s);
+/* Finish queued and running requests, stop the worker and free everything. */
+sws_status sws_server_destroy(sws_server *s);
+
 /* ---- minimizers without allocation ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that cannot allocate
  * device memory: code running inside a device-memory allocator's hooks (allocating there would

@@ -5,5 +5,5 @@ thin ctypes binding and ``synth`` the seeded input generators.  Importing the pa
 load the library; the first call does, and raises if it has not been built.
 """
 
-from .binding import (Batch, Context, SwsError, default_context, kmer_table, kmers, minimizers,  # noqa: F401
-                      minimizers_batch, minimizers_from_keys, sliding_sum)
+from .binding import (Batch, Context, Server, SwsError, default_context, kmer_table, kmers,  # noqa: F401
+                      minimizers, minimizers_batch, minimizers_from_keys, sliding_sum)

@@ -58,7 +58,25 @@ SIGNATURES = {
     "sws_batch_io_get": (i32, [vp, vp]),
     "sws_batch_run": (i32, [vp, u64, u64, vp]),
     "sws_batch_sync": (i32, [vp]),
+    "sws_server_create": (i32, [vp, vp, ctypes.POINTER(vp)]),
+    "sws_server_submit": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
+    "sws_server_wait": (i32, [vp, u64, ctypes.c_double, ctypes.POINTER(i32)]),
+    "sws_server_result": (i32, [vp, u64, vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]),
+    "sws_server_stats": (i32, [vp, vp]),
+    "sws_server_reset_stats": (i32, [vp]),
+    "sws_server_destroy": (i32, [vp]),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("k", i32), ("w", i32), ("mode", i32), ("slots", ctypes.c_uint32), ("max_requests_per_batch", u64),
+                ("max_bases_per_batch", u64), ("hbm_budget_bytes", u64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", u64), ("batches", u64), ("bases", u64), ("pending", u64), ("p50_s", ctypes.c_double),
+                ("p99_s", ctypes.c_double), ("max_s", ctypes.c_double), ("mean_s", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
 
 
 class BatchIO(ctypes.Structure):
@@ -344,3 +362,70 @@ class Batch:
         _check(load().sws_batch_sync(self.handle))
         c = int(self.count.item())
         return self.hash[:c], self.pos[:c], self.pick_offsets[: self.nreads + 1]
+
+
+class Server:
+    """Minimizer server with continuous batching (sws_server_*).  Requests are host sequences."""
+
+    def __init__(self, k: int, w: int, slots: int = 4, max_requests_per_batch: int = 256,
+                 max_bases_per_batch: int = 1 << 22, hbm_budget_bytes: int = 0, mode: str = "hash",
+                 ctx: Context | None = None):
+        import numpy as np  # noqa: F401  (results are numpy arrays)
+        self.ctx = ctx or default_context()
+        cfg = ServerConfig(k, w, MINI_MODES[mode], slots, max_requests_per_batch, max_bases_per_batch,
+                           hbm_budget_bytes)
+        h = vp()
+        _check(load().sws_server_create(self.ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self.w = w
+
+    def submit(self, packed, nbases: int) -> int:
+        """Queue one packed sequence (numpy uint8 array or CPU tensor); returns the request id."""
+        import numpy as np
+        arr = packed.numpy() if hasattr(packed, "numpy") else packed
+        arr = np.ascontiguousarray(arr, dtype=np.uint8)
+        rid = u64()
+        _check(load().sws_server_submit(self.handle, vp(arr.ctypes.data), int(nbases), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout: float = 60.0) -> bool:
+        done = i32()
+        _check(load().sws_server_wait(self.handle, int(rid), float(timeout), ctypes.byref(done)))
+        return bool(done.value)
+
+    def result(self, rid: int, capacity: int | None = None):
+        """(keys uint32, positions uint32, latency seconds) of an answered request."""
+        import numpy as np
+        cap = capacity if capacity is not None else 1 << 16
+        while True:
+            h = np.empty(max(cap, 1), dtype=np.uint32)
+            p = np.empty(max(cap, 1), dtype=np.uint32)
+            cnt = u64()
+            lat = ctypes.c_double()
+            st = load().sws_server_result(self.handle, int(rid), vp(h.ctypes.data), vp(p.ctypes.data), cap,
+                                          ctypes.byref(cnt), ctypes.byref(lat))
+            if st == SWS_ERR_CAPACITY and cnt.value > cap:
+                cap = int(cnt.value)
+                continue
+            _check(st)
+            c = int(cnt.value)
+            return h[:c], p[:c], float(lat.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().sws_server_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(load().sws_server_reset_stats(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.sws_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
