@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
-    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "batch"],
+    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "batch", "serve"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
@@ -284,6 +284,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extras and rank == 0:
         result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
         result["batched_reads"] = batch_extras(dev, ctx)
+        result["serving"] = serve_extras(ctx)
     del xs, outs
     torch.cuda.empty_cache()
     return result
@@ -458,6 +459,55 @@ def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain
             "speedup_batched_vs_plain": round(batched["gbp_s"] / max(plain_r["gbp_s"], 1e-9), 1)}
 
 
+def serve_extras(ctx, n_requests: int = 1500, loads=(0.5, 1.0, 1.5, 2.0), duration_s: float = 1.5):
+    """Serving: requests of log-uniform length in [150 bp, 1 Mbp] (k=15, w=10).  Capacity is the
+    throughput of a burst of all requests; then Poisson arrivals at fractions of it, p50/p99 of
+    submit-to-answer latency and the bases per second answered."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    lens = synth.loguniform_lengths(n_requests, 150, 1_000_000, seed=42)
+    starts = np.zeros(n_requests + 1, dtype=np.int64)
+    np.cumsum((lens + 3) // 4 * 4, out=starts[1:])
+    pool = synth.acgt_uniform_packed(int(starts[-1]), seed=43).numpy()
+    reqs = [(pool[starts[i] // 4: (starts[i] + lens[i] + 3) // 4], int(lens[i])) for i in range(n_requests)]
+    srv = P.Server(15, 10, slots=4, max_requests_per_batch=128, max_bases_per_batch=1 << 24, ctx=ctx)
+
+    def run(arrivals):
+        srv.reset_stats()
+        ids = []
+        t0 = time.perf_counter()
+        for i, at in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            ids.append((srv.submit(*reqs[i % n_requests]), reqs[i % n_requests][1]))
+        for rid, _ in ids:
+            srv.wait(rid, 120.0)
+            srv.result(rid)
+        st = srv.stats()
+        return st, sum(L for _, L in ids)
+
+    run([0.0] * 64)  # warm up
+    st, bases = run([0.0] * n_requests)
+    cap_bps = bases / st["span_s"]
+    mean_len = float(np.mean(lens))
+    out = {"workload": "requests log-uniform 150 bp - 1 Mbp, uniform ACGT, k=15 w=10; 4 slots, <=128 requests "
+                       "and <=16 Mbp per batch",
+           "capacity_gbp_s": round(cap_bps / 1e9, 3), "burst_requests": n_requests,
+           "burst_p50_ms": round(st["p50_s"] * 1e3, 3), "burst_p99_ms": round(st["p99_s"] * 1e3, 3), "loads": []}
+    for f in loads:
+        rate = f * cap_bps / mean_len
+        count = max(64, int(rate * duration_s))
+        arrivals = list(synth.poisson_arrivals(count, rate, seed=int(100 * f)))
+        st, bases = run(arrivals)
+        out["loads"].append({"offered_x_capacity": f, "requests": count, "arrival_rate_per_s": round(rate, 1),
+                             "p50_ms": round(st["p50_s"] * 1e3, 3), "p99_ms": round(st["p99_s"] * 1e3, 3),
+                             "max_ms": round(st["max_s"] * 1e3, 3), "gbp_s": round(bases / st["span_s"] / 1e9, 3),
+                             "batches": int(st["batches"])})
+    srv.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # reference arm: the oracle on host cores
 # ------------------------------------------------------------------------------------------
@@ -500,7 +550,7 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section in ("minimizers", "batch"):
+    if args.section in ("minimizers", "batch", "serve"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
@@ -509,8 +559,10 @@ def main():
         if rank == 0:
             if args.section == "minimizers":
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n)}), flush=True)
-            else:
+            elif args.section == "batch":
                 print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
+            else:
+                print(json.dumps({"serving": serve_extras(ctx)}), flush=True)
         return
     res = run_ours(args, world, rank, local)
     if rank == 0:
