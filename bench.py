@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
-    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "batch", "serve"],
+    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "table", "batch", "serve"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
@@ -265,10 +265,11 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "int32,u32x2,f32",
         "data": "synthetic (SplitMix64 seed 42, generated on the device)",
-        "config": {"workload": WORKLOAD, "n": n, "ops": OPS, "w": WS, "calls_per_step": len(cases),
+        "config": {"workload": WORKLOAD, "n": n, "ops": args.ops, "w": args.ws, "calls_per_step": len(cases),
                    "bytes_per_step": step_bytes, "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k_slide_bc (block-combine sliding sum, all operators)", "bound": "hbm",
+        "roofline": {"kernel": "sliding-sum block combine (k_slide_small for w=4, k_slide_al otherwise)",
+                     "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                      "traffic": None, "per_case_gbs": per_case},
@@ -279,10 +280,11 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt = cpu_baseline(args.cpu_sample)
         result["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                  "sample": f"{args.cpu_sample} elements per (op, w) case, all 30 cases, "
+                                  "sample": f"{args.cpu_sample} elements per (op, w) case, all {len(OPS) * len(WS)} cases, "
                                             f"{dt:.1f} s single-threaded naive O(wN)"}
     if not args.no_extras and rank == 0:
         result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
+        result["genome_table"] = genome_table_extras(dev, ctx)
         result["batched_reads"] = batch_extras(dev, ctx)
         result["serving"] = serve_extras(ctx)
     del xs, outs
@@ -386,6 +388,42 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
     b = 4 * m + 8 * picks
     out["sliding_min_keys_2^28_w10"] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
                                         "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    return out
+
+
+def genome_table_extras(dev, ctx, n: int = 3_100_000_000, reps: int = 3, bucket_bits: int = 24):
+    """Genome-scale seed table: a synthetic 3.1e9-base genome (GC 41% i.i.d., 5% of bases in
+    N-blocks of log-uniform length 10 kb - 1 Mb that break windows); for k=19 w=10 and k=15 w=50
+    the minimizers of the whole sequence, then the (hash, pos) hits radix-sorted into a table with
+    2^bucket_bits buckets.  Gbp/s counts genome bases over minimizers + table build."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    seq, iv = synth.genome_packed(n, device=dev)
+    nb = torch.from_numpy(iv).to(dev)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"{n} bases, GC 41%, {len(iv)} N-blocks covering {int((iv[:, 1] - iv[:, 0]).sum())} bases; "
+                       f"table of 2^{bucket_bits} buckets", "generate_s": round(gen_s, 1)}
+    for k, w in ((19, 10), (15, 50)):
+        cap = int(n * 2.6 / (w + 1)) + 1024
+        mini = lambda: P.minimizers(seq, n, k, w, nblocks=nb, capacity=cap, ctx=ctx, stream=stream, sync=False)
+        ms_m = time_call(mini, reps, stream)
+        h, p, cnt = mini()
+        m = int(cnt.item())
+        h, p = h[:m], p[:m]
+        tab = lambda: P.kmer_table(h, p, 2 * k, bucket_bits, ctx=ctx, stream=stream)
+        ms_t = time_call(tab, reps, stream)
+        hb = h.element_size()
+        out[f"k{k}_w{w}"] = {"hits": m, "minimizers_ms": round(ms_m, 2), "table_ms": round(ms_t, 2),
+                             "minimizers_gbp_s": round(n / (ms_m / 1e3) / 1e9, 1),
+                             "table_mhits_s": round(m / (ms_t / 1e3) / 1e6, 1),
+                             "gbp_s": round(n / ((ms_m + ms_t) / 1e3) / 1e9, 1),
+                             "hit_bytes": hb + 4}
+        del h, p, cnt
+        torch.cuda.empty_cache()
+    del seq, nb
+    torch.cuda.empty_cache()
     return out
 
 
@@ -550,7 +588,7 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section in ("minimizers", "batch", "serve"):
+    if args.section in ("minimizers", "table", "batch", "serve"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
@@ -559,6 +597,8 @@ def main():
         if rank == 0:
             if args.section == "minimizers":
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n)}), flush=True)
+            elif args.section == "table":
+                print(json.dumps({"genome_table": genome_table_extras(dev, ctx)}), flush=True)
             elif args.section == "batch":
                 print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
             else:

@@ -72,10 +72,18 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
 #define SWS_OP_ADD_F32 5
 
 /* Algorithm variants. */
-#define SWS_VARIANT_AUTO 0          /* tuned choice (see sws_tune)                              */
-#define SWS_VARIANT_BLOCK_COMBINE 1 /* blocks of w: in-block suffix + next-block prefix, O(1)/output */
+#define SWS_VARIANT_AUTO 0          /* the library's choice (block combine, streamed when it applies) */
+#define SWS_VARIANT_BLOCK_COMBINE 1 /* blocks of w: in-block suffix + next-block prefix, O(1)/output;
+                                       one-shot CTA tiles                                          */
 #define SWS_VARIANT_DOUBLING 2      /* ceil(log2 w) doubling levels, O(log w)/output            */
 #define SWS_VARIANT_PREFIX_DIFF 3   /* y_p = S_{p+w-1} - S_{p-1}; ADD_I32 and XOR_I32 only      */
+#define SWS_VARIANT_BLOCK_COMBINE_STREAM 4 /* block combine in a persistent kernel fed by 2-D TMA
+                                       copies; needs w = c*m with c = 16 (int32/fp32) or 8 (affine)
+                                       and m in {1,2,4,8,16,32} or a multiple of 32 (w <= 4096 int32,
+                                       <= 2048 affine), a 16-byte aligned input of at least 128
+                                       bytes, else SWS_ERR_UNSUPPORTED.  A copy that never completes within
+                                       about a second sets the context's error word (reported by
+                                       sws_sync as SWS_ERR_TIMEOUT).                               */
 
 /* Eq. 2: out[p] = in[p] (+) in[p+1] (+) ... (+) in[p+w-1] for p = 0 .. n-w (n-w+1 outputs,
  * exactly w addends each, Sec. 2.2).

@@ -167,7 +167,7 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   if (s) return s;
   if (op < SWS_OP_ADD_I32 || op > SWS_OP_ADD_F32) return fail(SWS_ERR_INVALID, "unknown operator %d", op);
   if (w < 1) return fail(SWS_ERR_INVALID, "w must be >= 1 (got %d)", w);
-  if (variant < SWS_VARIANT_AUTO || variant > SWS_VARIANT_PREFIX_DIFF)
+  if (variant < SWS_VARIANT_AUTO || variant > SWS_VARIANT_BLOCK_COMBINE_STREAM)
     return fail(SWS_ERR_INVALID, "unknown variant %d", variant);
   if (n < (uint64_t)w) return SWS_OK;
   if (!in || !out) return fail(SWS_ERR_INVALID, "in/out is NULL");
@@ -183,13 +183,18 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
     return fail(SWS_ERR_INVALID, "prefix-difference needs an invertible operator (ADD_I32 or XOR_I32)");
   sws::SlideLaunch L;
   L.op = op;
-  L.variant = variant == SWS_VARIANT_AUTO ? SWS_VARIANT_BLOCK_COMBINE : variant;
+  L.variant = variant;
+  L.num_sms = ctx->num_sms;
+  L.err = ctx->d_err;
   // the smaller tile when it keeps the halo re-read under an eighth of the tile
   const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
   L.cfg = (w - 1) * 8 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
   if (sws::slide_tile_outputs(L.cfg, es, w) == 0)
     return fail(SWS_ERR_UNSUPPORTED, "w = %d is larger than the tile of this build", w);
   cudaError_t e = sws::launch_sliding_sum(L, in, out, n, w, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorNotSupported && variant == SWS_VARIANT_BLOCK_COMBINE_STREAM)
+    return fail(SWS_ERR_UNSUPPORTED, "the streamed block combine does not apply to w = %d, n = %llu at this alignment",
+                w, (unsigned long long)n);
   if (e != cudaSuccess) return cuda_fail(e, "sliding-sum launch");
   return SWS_OK;
 }

@@ -20,8 +20,10 @@ enum SlideCfg { CFG_SMALL = 0, CFG_LARGE = 1, CFG_COUNT = 2 };
 
 struct SlideLaunch {
   int op;       // SWS_OP_*
-  int variant;  // SWS_VARIANT_BLOCK_COMBINE / DOUBLING / PREFIX_DIFF
+  int variant;  // SWS_VARIANT_*
   int cfg;      // SlideCfg
+  int num_sms;  // SMs of the device (grid of the persistent kernel)
+  int *err;     // device error word (bounded waits)
 };
 
 // Tile length (elements) of a configuration for elements of `esize` bytes.

@@ -58,10 +58,6 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {
   return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 struct Staging {
   long long gb0;   // global byte of staged byte 0
   long long lo;    // first byte of the bulk copy

@@ -12,14 +12,22 @@
 //                  output (Sec. 2.2 / Sec. 3.1: prefix scans inside each window).  Idempotent
 //                  operators finish with two overlapping 2^t windows; the others combine the
 //                  binary digits of w in order, which needs associativity only.
+//   block-combine, streamed   the same arithmetic for w a multiple of the thread chunk, in a
+//                  persistent kernel whose tiles arrive in shared memory by 2-D TMA copies
+//                  issued ahead of the compute (k_slide_tma).
 //   prefix-diff    for invertible operators (add mod 2^32, xor): y_p = T_{p+w-1} (-) T_{p-1},
 //                  with T the running sum from the tile start (the "recurrent" sliding sums of
 //                  Sec. 5), O(1) per output and independent of w.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/sws.h"
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace sws {
 
@@ -191,6 +199,179 @@ __global__ void __launch_bounds__(NT) k_slide_al(const typename Op::T *__restric
     for (int j = 1; j < VPT; ++j) y[j] = Op::op(S[j], Pn[j - 1]);
   }
   store_tile<Op, VPT>(out, n - (uint64_t)w + 1, g, t * VPT, TO, vec, y);
+}
+
+// ------------------------------------------------------------------------------------------
+// Block-combine, w a multiple of VPT, persistent, input staged by TMA
+// ------------------------------------------------------------------------------------------
+// The arithmetic of k_slide_al, fed differently.  A grid of a few CTAs per SM walks the tiles
+// round-robin; tile i's L inputs arrive in shared memory by one 2-D TMA copy (the array viewed
+// as rows of 128 bytes) issued STAGES tiles ahead on an mbarrier, so HBM sees a steady stream of
+// bulk reads while the threads scan.  The copy uses the 128-byte swizzle: 16-byte unit u of row
+// r lands at unit u ^ (r & 7), so the four units of thread t's 64-byte chunk (row t/2, units
+// 4(t&1) .. 4(t&1)+3) fall in eight distinct bank groups across every quarter-warp and the
+// reads are conflict free.  Tiles start at multiples of lcm(w, 128 bytes): whole blocks and
+// whole rows.  Elements of a final partial row are not in the tensor map (the copy fills them
+// with zeros); the threads that own them load them directly.  Every wait is bounded; on a
+// time-out the CTA flags DEVERR_COPY_TIMEOUT, lets its own copies land (bounded) and returns.
+constexpr int kStreamRowBytes = 128;
+constexpr int kStreamSpinLimit = 1 << 22;
+
+__device__ __forceinline__ bool stream_wait(unsigned long long *bar, uint32_t parity) {
+  for (int spins = 0; !tma::mbar_try_wait(bar, parity);) {
+    if (++spins > kStreamSpinLimit) return false;
+    if (spins > 64) __nanosleep(64);
+  }
+  return true;
+}
+
+template <class Op, int NT, int VPT, int STAGES, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_slide_tma(const __grid_constant__ CUtensorMap tmap, const typename Op::T *__restrict__ in,
+                typename Op::T *__restrict__ out, uint64_t n, uint64_t n_full, int w, int TO, uint64_t tiles,
+                int *err) {
+  using T = typename Op::T;
+  constexpr int NW = NT / 32;
+  constexpr int EPV = 16 / (int)sizeof(T);
+  constexpr int UPR = VPT / EPV;  // 16-byte units per thread chunk
+  constexpr int ROW = UPR + 1;    // padded row of the shared prefix array
+  constexpr int TILE_BYTES = NT * VPT * (int)sizeof(T);
+  static_assert(VPT * (int)sizeof(T) * 2 == kStreamRowBytes, "a thread chunk is half a 128-byte row");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[STAGES];
+  __shared__ T s_wf[NW], s_wb[NW];
+
+  unsigned char *stage0 = smem_raw + ((1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint4 *sm4 = reinterpret_cast<uint4 *>(stage0 + STAGES * TILE_BYTES);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int G = w / VPT;
+  const uint64_t rows_per_tile = (uint64_t)TO * sizeof(T) / kStreamRowBytes;
+  const uint64_t stride = gridDim.x;
+
+  if (t == 0) {
+    tma::prefetch_tensormap(&tmap);
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) tma::mbar_init(&full[s], 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) {
+      const uint64_t tile = blockIdx.x + (uint64_t)s * stride;
+      if (tile < tiles) {
+        tma::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+        tma::tensor_g2s_2d(stage0 + s * TILE_BYTES, &tmap, 0, (int)(tile * rows_per_tile), &full[s]);
+      }
+    }
+  }
+  const bool vec = aligned16(out);
+  const uint64_t nout = n - (uint64_t)w + 1;
+  int it = 0;
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += stride, ++it) {
+    const int s = it % STAGES;
+    const bool ok = stream_wait(&full[s], (uint32_t)(it / STAGES) & 1u);
+    T x[VPT];
+    if (ok) {
+      const unsigned char *src = stage0 + s * TILE_BYTES + (t >> 1) * kStreamRowBytes;
+      const int sw = (t >> 1) & 7;
+      uint4 u[UPR];
+#pragma unroll
+      for (int c = 0; c < UPR; ++c) u[c] = *reinterpret_cast<const uint4 *>(src + ((((t & 1) * UPR + c) ^ sw) << 4));
+      memcpy(x, u, sizeof(u));
+    }
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) {
+        atomicOr(err, DEVERR_COPY_TIMEOUT);
+        // let every copy this CTA still has in flight land before it exits (bounded)
+        for (int j = 0; j < STAGES; ++j) {
+          const uint64_t tj = tile + (uint64_t)j * stride;
+          if (tj < tiles) stream_wait(&full[(it + j) % STAGES], (uint32_t)((it + j) / STAGES) & 1u);
+        }
+      }
+      return;
+    }
+    if (t == 0) {
+      const uint64_t nt = tile + (uint64_t)STAGES * stride;
+      if (nt < tiles) {
+        tma::fence_proxy_async_smem();
+        tma::mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+        tma::tensor_g2s_2d(stage0 + s * TILE_BYTES, &tmap, 0, (int)(nt * rows_per_tile), &full[s]);
+      }
+    }
+    const uint64_t g = tile * (uint64_t)TO + (uint64_t)t * VPT;
+    if (g + VPT > n_full) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j)
+        if (g + j >= n_full) x[j] = (g + j < n) ? in[g + j] : Op::identity();
+    }
+
+    T P[VPT], S[VPT];
+    P[0] = x[0];
+#pragma unroll
+    for (int j = 1; j < VPT; ++j) P[j] = Op::op(P[j - 1], x[j]);
+    S[VPT - 1] = x[VPT - 1];
+#pragma unroll
+    for (int j = VPT - 2; j >= 0; --j) S[j] = Op::op(x[j], S[j + 1]);
+
+    const int pos = t % G;
+    const bool head = pos == 0, tail = pos == G - 1;
+    T cP, cS;
+    if (G <= 32) {
+      T vf = P[VPT - 1], vb = S[0];
+      for (int d = 1; d < G; d <<= 1) {
+        const T a = shfl_up_t(vf, d);
+        const T b = shfl_down_t(vb, d);
+        if (pos >= d) vf = Op::op(a, vf);
+        if (pos + d < G) vb = Op::op(vb, b);
+      }
+      cP = shfl_up_t(vf, 1);
+      cS = shfl_down_t(vb, 1);
+    } else {
+      const int m = G >> 5, wp = warp % m;
+      const T vf = warp_seg_scan_fwd<Op>(P[VPT - 1], 0u, lane);
+      const T vb = warp_seg_scan_bwd<Op>(S[0], 0u, lane);
+      if (lane == 31) s_wf[warp] = vf;
+      if (lane == 0) s_wb[warp] = vb;
+      __syncthreads();
+      const T ef = shfl_up_t(vf, 1);
+      const T eb = shfl_down_t(vb, 1);
+      T cwf = Op::identity(), cwb = Op::identity();
+      for (int i = warp - wp; i < warp; ++i) cwf = (i == warp - wp) ? s_wf[i] : Op::op(cwf, s_wf[i]);
+      for (int i = warp - wp + m - 1; i > warp; --i) cwb = (i == warp - wp + m - 1) ? s_wb[i] : Op::op(s_wb[i], cwb);
+      cP = lane == 0 ? cwf : (wp > 0 ? Op::op(cwf, ef) : ef);
+      cS = lane == 31 ? cwb : (wp < m - 1 ? Op::op(eb, cwb) : eb);
+    }
+    if (!head) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) P[j] = Op::op(cP, P[j]);
+    }
+    if (!tail) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) S[j] = Op::op(S[j], cS);
+    }
+    {
+      uint4 u[UPR];
+      memcpy(u, P, sizeof(u));
+#pragma unroll
+      for (int c = 0; c < UPR; ++c) sm4[t * ROW + c] = u[c];
+    }
+    __syncthreads();
+    T y[VPT];
+    {
+      const int tn = t + G < NT ? t + G : NT - 1;  // past the tile only for outputs beyond TO
+      uint4 u[UPR];
+#pragma unroll
+      for (int c = 0; c < UPR; ++c) u[c] = sm4[tn * ROW + c];
+      T Pn[VPT];
+      memcpy(Pn, u, sizeof(u));
+      const T plast = reinterpret_cast<const T *>(sm4 + (tn - 1) * ROW)[VPT - 1];
+      y[0] = head ? S[0] : Op::op(S[0], plast);
+#pragma unroll
+      for (int j = 1; j < VPT; ++j) y[j] = Op::op(S[j], Pn[j - 1]);
+    }
+    store_tile<Op, VPT>(out, nout, g, t * VPT, TO, vec, y);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -416,10 +597,107 @@ cudaError_t set_smem(Kern kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// ---- persistent TMA-staged block-combine ---------------------------------------------------
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no -lcuda).
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+int gcd_int(int a, int b) {
+  while (b) {
+    const int r = a % b;
+    a = b;
+    b = r;
+  }
+  return a;
+}
+
+// Outputs per tile of the streamed kernel: the largest multiple of lcm(w, elements per 128-byte
+// row) that leaves the tile room for the following block; 0 when none fits.
+int stream_tile_outputs(int L, int esize, int w) {
+  const long long r = kStreamRowBytes / esize;
+  const long long unit = (long long)w / gcd_int(w, (int)r) * r;
+  return (int)((L - w + 1) / unit * unit);
+}
+
+template <class Op, int NT, int VPT, int MINB>
+cudaError_t launch_stream(const void *in, void *out, uint64_t n, int w, int num_sms, int *err, cudaStream_t st,
+                          bool quiet_unsupported) {
+  using T = typename Op::T;
+  constexpr int STAGES = 2;
+  constexpr int L = NT * VPT;
+  constexpr int ES = (int)sizeof(T);
+  constexpr int ROW = VPT * ES / 16 + 1;
+  static_assert(L * ES / kStreamRowBytes <= 256, "a TMA box has at most 256 rows");
+  const int TO = stream_tile_outputs(L, ES, w);
+  const uint64_t rows = n * ES / kStreamRowBytes;
+  const uint64_t nout = n - (uint64_t)w + 1;
+  const uint64_t tiles = TO > 0 ? (nout + (uint64_t)TO - 1) / (uint64_t)TO : 0;
+  EncodeTiled enc = encode_tiled();
+  if (TO == 0 || rows == 0 || rows > (1ull << 32) || (reinterpret_cast<uintptr_t>(in) & 15u) != 0 ||
+      !aligned_blocks_ok(w, VPT, NT, L) || !enc || num_sms < 1 || err == nullptr ||
+      tiles * (uint64_t)TO * ES / kStreamRowBytes > 0x7fffffffull)
+    return quiet_unsupported ? cudaErrorNotSupported : cudaErrorInvalidValue;
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {kStreamRowBytes / 4, rows};
+  const cuuint64_t gstride[1] = {kStreamRowBytes};
+  const cuuint32_t box[2] = {kStreamRowBytes / 4, (cuuint32_t)(L * ES / kStreamRowBytes)};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(in), gdim, gstride, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)STAGES * L * ES + (size_t)NT * ROW * 16 + 1024;
+  auto kern = k_slide_tma<Op, NT, VPT, STAGES, MINB>;
+  // resident CTAs per SM, once per device (the attribute and the answer do not change)
+  static int per_sm[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
+  if (nb == 0) {
+    e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) per_sm[dev] = nb;
+  }
+  uint64_t grid = (uint64_t)num_sms * (uint64_t)nb;
+  if (grid > tiles) grid = tiles;
+  const uint64_t n_full = rows * kStreamRowBytes / ES;
+  kern<<<(unsigned)grid, NT, smem, st>>>(map, static_cast<const T *>(in), static_cast<T *>(out), n, n_full, w, TO,
+                                         tiles, err);
+  return cudaGetLastError();
+}
+
 template <class Op, class Cfg>
-cudaError_t launch_op(int variant, const void *in, void *out, uint64_t n, int w, cudaStream_t st) {
+cudaError_t launch_op(const SlideLaunch &SL, const void *in, void *out, uint64_t n, int w, cudaStream_t st) {
   using T = typename Op::T;
   using S = Shape<Cfg, (int)sizeof(T)>;
+  constexpr int MINB = 1024 / S::NT;
+  const int variant = SL.variant;
+  if (variant == SWS_VARIANT_BLOCK_COMBINE_STREAM)
+    return launch_stream<Op, S::NT, S::VPT, MINB>(in, out, n, w, SL.num_sms, SL.err, st, true);
+  if (variant == SWS_VARIANT_AUTO && !(w <= 8 && S::VPT % w == 0)) {
+    // streamed when the grid fills the GPU at least twice; the one-shot tiles otherwise
+    const int TOs = stream_tile_outputs(S::L, (int)sizeof(T), w);
+    if (TOs > 0 && (n - (uint64_t)w + 1) / (uint64_t)TOs >= 2ull * (uint64_t)SL.num_sms * (uint64_t)MINB) {
+      const cudaError_t e = launch_stream<Op, S::NT, S::VPT, MINB>(in, out, n, w, SL.num_sms, SL.err, st, true);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   const int TO = tile_outputs(S::L, (int)sizeof(T), w);
   if (TO == 0) return cudaErrorInvalidValue;
   const uint64_t nout = n - (uint64_t)w + 1;
@@ -487,12 +765,12 @@ cudaError_t launch_cfg(const SlideLaunch &L, const void *in, void *out, uint64_t
     return cudaErrorInvalidValue;
   }
   switch (L.op) {
-    case SWS_OP_ADD_I32: return launch_op<OpAddI32, Cfg>(L.variant, in, out, n, w, st);
-    case SWS_OP_MIN_I32: return launch_op<OpMinI32, Cfg>(L.variant, in, out, n, w, st);
-    case SWS_OP_MAX_I32: return launch_op<OpMaxI32, Cfg>(L.variant, in, out, n, w, st);
-    case SWS_OP_XOR_I32: return launch_op<OpXorI32, Cfg>(L.variant, in, out, n, w, st);
-    case SWS_OP_AFFINE_U32: return launch_op<OpAffineU32, Cfg>(L.variant, in, out, n, w, st);
-    case SWS_OP_ADD_F32: return launch_op<OpAddF32, Cfg>(L.variant, in, out, n, w, st);
+    case SWS_OP_ADD_I32: return launch_op<OpAddI32, Cfg>(L, in, out, n, w, st);
+    case SWS_OP_MIN_I32: return launch_op<OpMinI32, Cfg>(L, in, out, n, w, st);
+    case SWS_OP_MAX_I32: return launch_op<OpMaxI32, Cfg>(L, in, out, n, w, st);
+    case SWS_OP_XOR_I32: return launch_op<OpXorI32, Cfg>(L, in, out, n, w, st);
+    case SWS_OP_AFFINE_U32: return launch_op<OpAffineU32, Cfg>(L, in, out, n, w, st);
+    case SWS_OP_ADD_F32: return launch_op<OpAddF32, Cfg>(L, in, out, n, w, st);
     default: return cudaErrorInvalidValue;
   }
 }

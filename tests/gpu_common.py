@@ -88,3 +88,33 @@ def random_nblocks(n: int, rng: np.random.Generator, count: int, maxlen: int) ->
         iv.append((s, e))
         last_end = e + 1
     return np.array(iv, dtype=np.int64).reshape(-1, 2)
+
+
+def sample_indices(m: int, rng: np.random.Generator, count: int = 2048) -> np.ndarray:
+    """Output indices to check on a large sliding sum: both ends, tile seams, random."""
+    parts = [np.arange(min(64, m)), np.arange(max(m - 64, 0), m)]
+    for tile in (4096, 8192):
+        seams = rng.integers(1, max(m // tile, 2), size=32) * tile
+        parts.append((seams[:, None] + np.arange(-3, 3)[None, :]).ravel())
+    parts.append(rng.integers(0, m, size=count))
+    idx = np.unique(np.concatenate(parts))
+    return idx[(idx >= 0) & (idx < m)]
+
+
+def assert_sampled(op: str, w: int, x: torch.Tensor, y: torch.Tensor, idx: np.ndarray):
+    """y (device) against the oracle evaluated window by window at the sampled outputs idx."""
+    dev = x.device
+    it = torch.from_numpy(idx).to(dev)
+    yv = y[it].cpu().numpy()
+    win = x[it[:, None] + torch.arange(w, device=dev)[None, :]].cpu()
+    flat = win.reshape((-1,) + tuple(x.shape[1:]))
+    ref = oracle.sliding_sum_at(op, w, flat, np.arange(idx.size, dtype=np.uint64) * w)
+    if op == "add_f32":
+        bound = np.abs(win.numpy().astype(np.float64)).sum(axis=1)
+        err = np.abs(yv.astype(np.float64) - ref)
+        bad = np.nonzero(err > FP32_TOL * np.maximum(np.abs(ref), bound))[0]
+    elif op == "affine_u32":
+        bad = np.nonzero((yv.view(np.uint32).reshape(-1, 2) != ref).any(axis=1))[0]
+    else:
+        bad = np.nonzero(yv != ref)[0]
+    assert bad.size == 0, (op, w, idx[bad[:5]])

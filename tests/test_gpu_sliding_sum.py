@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from paper_1811_10074_gb300 import binding as B
-from gpu_common import assert_sliding_equal, make_input, oracle_sliding, require_gpu
+from gpu_common import assert_sampled, assert_sliding_equal, make_input, oracle_sliding, require_gpu, sample_indices
 
 pytestmark = pytest.mark.gpu
 
@@ -80,3 +80,56 @@ def test_invalid_arguments_are_rejected():
         B.sliding_sum("min_i32", 4, x, variant="prefix_diff")
     with pytest.raises(B.SwsError, match="INVALID"):
         B.sliding_sum("add_i32", 4, x, out=x[:97])  # overlapping
+
+
+# ---------------------------------------------------------------------------------------------
+# the persistent TMA-fed block combine ("stream")
+# ---------------------------------------------------------------------------------------------
+def stream_ws(op):
+    c = 8 if op == "affine_u32" else 16
+    return [c, 2 * c, 4 * c, 16 * c, 32 * c, 64 * c, 128 * c]
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_stream_variant_matches_oracle(op):
+    """Every block shape (blocks inside a warp, whole warps), one tile to many, a ragged tail
+    that ends inside a 128-byte row (those elements bypass the tensor copy)."""
+    for w in stream_ws(op):
+        for n in (w + 40, 4096 + 7, 3 * 8192 + 17, 100_003):
+            if n < w:
+                continue
+            x, ref = oracle_sliding(op, w, n, 11, op in INT_OPS)
+            y = B.sliding_sum(op, w, x.cuda(), variant="stream")
+            torch.cuda.synchronize()
+            assert_sliding_equal(op, w, x, y, ref)
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_stream_variant_many_tiles_per_cta(op):
+    """Enough tiles that every CTA cycles its two stages many times (mbarrier phases wrap)."""
+    rng = np.random.default_rng(3)
+    n = (1 << 23) + 13
+    x = make_input(op, n, seed=5, device="cuda")
+    for w in stream_ws(op)[::2]:
+        y = B.sliding_sum(op, w, x, variant="stream")
+        yb = B.sliding_sum(op, w, x, variant="block_combine")
+        torch.cuda.synchronize()
+        if op != "add_f32":
+            assert torch.equal(y, yb), (op, w)
+        assert_sampled(op, w, x, y, sample_indices(n - w + 1, rng, 4096))
+
+
+@pytest.mark.parametrize("op", ["add_i32", "affine_u32"])
+def test_stream_variant_unsupported_shapes(op):
+    c = 8 if op == "affine_u32" else 16
+    x = make_input(op, 1 << 23, device="cuda")
+    with pytest.raises(B.SwsError, match="UNSUPPORTED"):
+        B.sliding_sum(op, 3 * c, x, variant="stream")  # 3 chunks per block
+    with pytest.raises(B.SwsError, match="UNSUPPORTED"):
+        B.sliding_sum(op, 4 * c, x[1:], variant="stream")  # input not 16-byte aligned
+    with pytest.raises(B.SwsError, match="UNSUPPORTED"):
+        B.sliding_sum(op, c, x[: c + 4], variant="stream")  # less than one 128-byte row
+    # the automatic choice falls back to the one-shot tiles for the unaligned view
+    y = B.sliding_sum(op, 4 * c, x[1:])
+    torch.cuda.synchronize()
+    assert_sampled(op, 4 * c, x[1:], y, sample_indices(y.shape[0], np.random.default_rng(1)))
