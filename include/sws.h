@@ -85,6 +85,15 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
                                        about a second sets the context's error word (reported by
                                        sws_sync as SWS_ERR_TIMEOUT).                               */
 
+/* Failure detection self-test (no counterpart in the paper).  Queues one warp that runs one of
+ * the library's bounded device-side waits against a flag that nothing ever sets:
+ *   which = 0 : the look-back poll (a predecessor tile whose status word stays zero);
+ *   which = 1 : an mbarrier wait for 16 bytes of a TMA copy that is never issued.
+ * The wait gives up after about a second, records the time-out in the context's error word and
+ * returns; the next sws_sync on that stream returns SWS_ERR_TIMEOUT (and clears the word) and the
+ * context stays usable.  Nothing faults, traps or hangs.  which outside {0, 1}: SWS_ERR_INVALID. */
+sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream);
+
 /* Eq. 2: out[p] = in[p] (+) in[p+1] (+) ... (+) in[p+w-1] for p = 0 .. n-w (n-w+1 outputs,
  * exactly w addends each, Sec. 2.2).
  *   in, out : device arrays of n and n-w+1 elements of the operator's type; must not overlap;

@@ -47,6 +47,7 @@ SIGNATURES = {
     "sws_reserve": (i32, [vp, u64]),
     "sws_sync": (i32, [vp, vp]),
     "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
+    "sws_selftest_wait_timeout": (i32, [vp, i32, vp]),
     "sws_kmers": (i32, [vp, vp, u64, i32, i32, vp, vp]),
     "sws_minimizers": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
     "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
@@ -192,6 +193,13 @@ def sliding_sum(op: str, w: int, x: torch.Tensor, out: torch.Tensor | None = Non
     _check(load().sws_sliding_sum(ctx.handle, OPS[op], int(w), _ptr(x), _ptr(out), n, VARIANTS[variant],
                                   _stream(stream)))
     return out
+
+
+def selftest_wait_timeout(which: str = "lookback", ctx: Context | None = None, stream=None) -> None:
+    """Queue a bounded device wait on a flag nothing sets ("lookback" or "mbarrier"); the next
+    ``Context.sync`` raises SwsError(TIMEOUT)."""
+    ctx = ctx or default_context(torch.cuda.current_device())
+    _check(load().sws_selftest_wait_timeout(ctx.handle, {"lookback": 0, "mbarrier": 1}[which], _stream(stream)))
 
 
 def kmers(seq: torch.Tensor, n: int, k: int, kind: str = "hash", out: torch.Tensor | None = None,

@@ -161,6 +161,19 @@ sws_status sws_sync(sws_ctx *ctx, void *stream) {
   return SWS_OK;
 }
 
+sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (which != 0 && which != 1) return fail(SWS_ERR_INVALID, "which must be 0 (look-back) or 1 (mbarrier)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // two status words after the error word in the context's error block (zero = never written)
+  unsigned long long *status = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(ctx->d_err) + 64);
+  SWS_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(unsigned long long), st));
+  cudaError_t e = sws::launch_selftest_wait(which, status, ctx->d_err, st);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+  return SWS_OK;
+}
+
 sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *out, uint64_t n, int variant,
                            void *stream) {
   sws_status s = enter(ctx);

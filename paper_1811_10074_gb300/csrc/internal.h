@@ -133,4 +133,8 @@ int check_minimizer_args(int k, int w, int mode);
 // Device error bits.
 enum DevErr { DEVERR_LOOKBACK_TIMEOUT = 1, DEVERR_COPY_TIMEOUT = 2 };
 
+// One warp running a bounded wait on a flag nothing sets (0: look-back poll on `status`, two
+// zeroed words; 1: an mbarrier expecting bytes that never arrive); records the time-out in err.
+cudaError_t launch_selftest_wait(int which, unsigned long long *status, int *err, cudaStream_t st);
+
 }  // namespace sws

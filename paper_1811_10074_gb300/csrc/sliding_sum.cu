@@ -218,11 +218,7 @@ constexpr int kStreamRowBytes = 128;
 constexpr int kStreamSpinLimit = 1 << 22;
 
 __device__ __forceinline__ bool stream_wait(unsigned long long *bar, uint32_t parity) {
-  for (int spins = 0; !tma::mbar_try_wait(bar, parity);) {
-    if (++spins > kStreamSpinLimit) return false;
-    if (spins > 64) __nanosleep(64);
-  }
-  return true;
+  return tma::mbar_wait_bounded(bar, parity, kStreamSpinLimit);
 }
 
 template <class Op, int NT, int VPT, int STAGES, int MINB>

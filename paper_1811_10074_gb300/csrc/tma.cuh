@@ -54,6 +54,15 @@ __device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map,
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// Wait for the phase of `bar` with the given parity: spin briefly, then poll with a short sleep,
+// and give up after `limit` polls (about a second at 2^22).  Returns false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, int limit) {
+  for (int spins = 0; !mbar_try_wait(bar, parity);) {
+    if (++spins > limit) return false;
+    if (spins > 64) __nanosleep(64);
+  }
+  return true;
+}
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
