@@ -8,7 +8,7 @@
 //      count to a per-tile word.  The next tile's packed bases are fetched by TMA (cp.async.bulk
 //      into the other of two shared buffers, completed on an mbarrier) while this one computes.
 //   2. an exclusive scan of the per-tile counts (scan_u32 in table.cu);
-//   3. k_mini_gather: each warp copies one tile's picks to their final, position-ordered place.
+//   3. k_mini_gather: each CTA copies one tile's picks to their final, position-ordered place.
 //
 // The staging costs about 16 bytes of traffic per pick; in exchange no CTA ever waits for another
 // (the single-kernel path in minimizer.cu orders its output with a look-back instead).
@@ -47,8 +47,8 @@ struct Geo {
   static constexpr int L = FNT * VPT;            // k-mers per tile
   static constexpr int TW = (FNT * NB - 2) * W;  // windows per tile (a multiple of w)
   static constexpr int STAGE = SRC == SRC_DNA ? ((63 + L + 16) / 4 + 16 + 15) / 16 * 16 : (L + 8) * 4;
-  static constexpr int OFF_SX = 2 * STAGE;  // keys of the tile: sx[o + 1]
-  static constexpr int OFF_BAR = OFF_SX + ((L + 2) * 4 + 15) / 16 * 16;
+  static constexpr int OFF_SX = 2 * STAGE;  // DNA: keys of the tile, sx[o + 1] (keys: read from the stage)
+  static constexpr int OFF_BAR = OFF_SX + (SRC == SRC_DNA ? ((L + 2) * 4 + 15) / 16 * 16 : 0);
   static constexpr int OFF_PICKS = OFF_BAR + FMAXB * 16;
   static constexpr int PICK_WORDS = BAR == BAR_READS ? 3 : 2;
   static constexpr int BYTES = OFF_PICKS + TW * 4 * PICK_WORDS;
@@ -143,10 +143,20 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       }
       phases ^= 1u << b;
     }
-    for (int i = t; i < G::STAGE; i += FNT) {
-      const long long g = stg.gb0 + i;
-      if (g >= stg.lo && g < stg.lo + stg.bulk) continue;
-      stage[i] = (g >= 0 && g < (long long)nbytes) ? src[g] : (uint8_t)0;
+    {
+      // bytes the bulk copy did not bring: [0, head) and [tail, STAGE) of the stage
+      const int head = (int)(stg.lo - stg.gb0), tail = (int)(stg.lo + stg.bulk - stg.gb0);
+      const int nhead = stg.bulk > 0 ? head : G::STAGE;
+      for (int i = t; i < nhead; i += FNT) {
+        const long long g = stg.gb0 + i;
+        stage[i] = (g >= 0 && g < (long long)nbytes) ? src[g] : (uint8_t)0;
+      }
+      if (stg.bulk > 0) {
+        for (int i = tail + t; i < G::STAGE; i += FNT) {
+          const long long g = stg.gb0 + i;
+          stage[i] = (g < (long long)nbytes) ? src[g] : (uint8_t)0;
+        }
+      }
     }
     uint32_t g_lo = 0, nb = 0;
     if (tile_bar != nullptr) {
@@ -204,9 +214,17 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 #pragma unroll
       for (int j = 0; j < VPT; ++j) x[j] = (j >= jlo && j < jhi) ? sk[r + j] : 0xFFFFFFFFu;
     }
+    // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
+    // tile's keys go through shared memory; precomputed keys are read from the stage directly.
+    const uint32_t *kx;  // kx[o]: key of tile-local k-mer o
+    if (SRC == SRC_DNA) {
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
-    __syncthreads();
+      for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
+      __syncthreads();
+      kx = sx + 1;
+    } else {
+      kx = reinterpret_cast<const uint32_t *>(stage) + (i0 - stg.gb0 / 4);
+    }
 
     // ---- window minima and their leftmost positions, by block-combine on registers -----------
     // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
@@ -214,8 +232,8 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     // its prefix part, so ties between the two go to the suffix.
     uint32_t xn[WM1];  // the next thread's first w-1 keys
 #pragma unroll
-    for (int i = 0; i < W - 1; ++i) xn[i] = sx[1 + (t + 1 < FNT ? t + 1 : t) * VPT + i];
-    const uint32_t xprev = sx[t * VPT];  // key of k-mer ifirst - 1 (unused for thread 0)
+    for (int i = 0; i < W - 1; ++i) xn[i] = kx[(t + 1 < FNT ? t + 1 : t) * VPT + i];
+    const uint32_t xprev = t > 0 ? kx[t * VPT - 1] : 0xFFFFFFFFu;  // key of k-mer ifirst - 1 (unused for thread 0)
     const int o0 = t * VPT;
     uint32_t P[VPT], S[VPT], Pp[VPT], Sp[VPT], Pn[WM1], Pnp[WM1], y[VPT], yp[VPT];
 #pragma unroll
@@ -365,26 +383,42 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
   }
 }
 
-// Step 3: one warp per tile copies its staged picks to their place (offsets = scanned counts).
+// Step 3: one CTA per tile copies its staged picks to their place (offsets = scanned counts).
+// Each thread loads up to four picks before it stores any, so a CTA keeps many independent
+// requests in flight (the copy is latency bound otherwise).
+constexpr int GNT = 256, GUNROLL = 4;
+
 template <int BAR>
-__global__ void k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
+__global__ void __launch_bounds__(GNT) k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
   if (a.desc) num_tiles = (uint32_t)a.desc[BD_TILES];
-  const uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = a.tile_counts[num_tiles];
-  if (tile >= num_tiles) return;
-  const uint32_t o = a.tile_counts[tile], c = a.tile_counts[tile + 1] - o;
-  const uint64_t slot = tile * (uint64_t)TW;
   uint32_t *gh = static_cast<uint32_t *>(a.hash_out);
-  for (uint32_t i = lane; i < c; i += 32) {
-    const uint64_t gi = (uint64_t)o + i;
-    if (gi < a.capacity) {
-      gh[gi] = a.stg_hash[slot + i];
-      a.pos_out[gi] = a.stg_pos[slot + i];
-    }
-    if (BAR == BAR_READS) {
-      const uint32_t rd = a.stg_first[slot + i];
-      if (rd != 0xFFFFFFFFu) a.pick_offsets[rd] = gi;
+  for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+    const uint32_t o = a.tile_counts[tile], c = a.tile_counts[tile + 1] - o;
+    const uint64_t slot = tile * (uint64_t)TW;
+    for (uint32_t b = 0; b < c; b += GNT * GUNROLL) {
+      uint32_t h[GUNROLL], p[GUNROLL], f[GUNROLL];
+#pragma unroll
+      for (int u = 0; u < GUNROLL; ++u) {
+        const uint32_t i = b + u * GNT + threadIdx.x;
+        if (i < c) {
+          h[u] = a.stg_hash[slot + i];
+          p[u] = a.stg_pos[slot + i];
+          f[u] = BAR == BAR_READS ? a.stg_first[slot + i] : 0xFFFFFFFFu;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < GUNROLL; ++u) {
+        const uint32_t i = b + u * GNT + threadIdx.x;
+        if (i < c) {
+          const uint64_t gi = (uint64_t)o + i;
+          if (gi < a.capacity) {
+            gh[gi] = h[u];
+            a.pos_out[gi] = p[u];
+          }
+          if (BAR == BAR_READS && f[u] != 0xFFFFFFFFu) a.pick_offsets[f[u]] = gi;
+        }
+      }
     }
   }
 }
@@ -460,9 +494,9 @@ cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier,
   if (a.desc) e = scan_u32_dev(a.tile_counts, num_tiles + 1, a.desc + BD_SCAN_LEN, a.scan_tmp, st);
   else e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
-  const uint64_t blocks = (num_tiles * 32 + 255) / 256;
-  if (barrier == BAR_READS) k_mini_gather<BAR_READS><<<(unsigned)blocks, 256, 0, st>>>(a, (uint32_t)num_tiles, TW);
-  else k_mini_gather<BAR_NBLOCK><<<(unsigned)blocks, 256, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  const unsigned blocks = (unsigned)(num_tiles < (1u << 20) ? num_tiles : (1u << 20));
+  if (barrier == BAR_READS) k_mini_gather<BAR_READS><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  else k_mini_gather<BAR_NBLOCK><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,20 @@ def test_minimizers_with_nblocks(k, w):
         check_minimizers(seq, n, k, w, "hash", iv)
 
 
+def test_minimizers_low_complexity_ties_staged():
+    """A repetitive sequence long enough for the staged kernel (more than 4 tiles per SM), with
+    N-blocks: equal keys everywhere, the leftmost must win."""
+    unit = synth.codes_from_string("ACGTTGCAACGGA")
+    codes = unit.repeat(200_000)
+    codes[12345] = 3
+    seq = synth.pack_codes(codes)
+    n = codes.numel()
+    rng = np.random.default_rng(8)
+    for k, w, mode in ((15, 10, "hash"), (5, 4, "fwd"), (9, 16, "canonical")):
+        check_minimizers(seq, n, k, w, mode)
+        check_minimizers(seq, n, k, w, mode, random_nblocks(n, rng, 300, 40))
+
+
 def test_minimizers_low_complexity_ties():
     """A repetitive sequence makes many equal keys: the leftmost must win everywhere."""
     unit = synth.codes_from_string("ACGTTGCAAC")
@@ -155,3 +169,59 @@ def test_specialized_window_lengths(w):
     rh, rp, rpo = oracle.minimizers_batch(bseq, offs, 15, w)
     assert (bpo.cpu().numpy().view(np.uint64) == rpo).all()
     assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
+
+
+# Edge cases of the values-only pick rule (a new pick iff the previous window's first key was its
+# minimum, or the entering key is strictly smaller), on both paths: inputs of a few tiles take the
+# look-back kernel, inputs of 700 tiles the staged kernel.
+@pytest.mark.parametrize("w", [4, 5, 7, 8, 10, 13, 16])
+def test_key_minimizers_edge_cases(w):
+    rng = np.random.default_rng(77 + w)
+    tw = (256 * (16 // w) - 2) * w
+    cases = {
+        "short": rng.integers(0, 1 << 30, size=w, dtype=np.int64),
+        "w+1": rng.integers(0, 1 << 30, size=w + 1, dtype=np.int64),
+        "tile-1": rng.integers(0, 1 << 30, size=tw + w - 2, dtype=np.int64),
+        "tile+1": rng.integers(0, 1 << 30, size=tw + w, dtype=np.int64),
+        "increasing": np.arange(5 * tw + 3, dtype=np.int64),            # every pick leaves by expiry
+        "decreasing": np.arange(5 * tw + 3, 0, -1, dtype=np.int64),     # every entering key is smaller
+        "few values": rng.integers(0, 3, size=7 * tw + 11, dtype=np.int64),  # ties everywhere
+        "constant": np.full(3 * tw + 5, 12345, dtype=np.int64),
+        "full range": rng.integers(0, 1 << 32, size=50 * tw + 7, dtype=np.int64),
+        "increasing, staged": np.arange(700 * tw + 3, dtype=np.int64),
+        "decreasing, staged": np.arange(700 * tw + 3, 0, -1, dtype=np.int64),
+        "few values, staged": rng.integers(0, 3, size=700 * tw + 11, dtype=np.int64),
+        "sawtooth, staged": np.arange(700 * tw + 5, dtype=np.int64) % (3 * w + 1),
+    }
+    for name, k64 in cases.items():
+        keys = k64.astype(np.uint32)
+        kd = torch.from_numpy(keys.view(np.int32)).cuda()
+        for view in ("aligned", "offset"):
+            kv = kd if view == "aligned" else torch.cat([kd[:1], kd])[1:]  # 4-byte aligned only
+            h, p = B.minimizers_from_keys(kv, w)
+            rh, rp = oracle.minimizers_from_keys(keys.astype(np.uint64), w)
+            assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all(), (w, name, view)
+
+
+def test_key_minimizers_full_size_sampled():
+    """2^28 uniform 30-bit keys, w = 10 (the benchmark's configuration): the picks whose key lies
+    at least w keys inside a segment depend only on that segment."""
+    m, w = 1 << 28, 10
+    keys = synth.uint32_hashes(m, device="cuda")
+    h, p, cnt = B.minimizers_from_keys(keys, w, capacity=m // 4, sync=False)
+    count = int(cnt.item())
+    assert abs(count / m - 2 / (w + 1)) < 0.01
+    pos = p[:count].to(torch.int64) & 0xFFFFFFFF
+    assert bool((pos[1:] > pos[:-1]).all())
+    rng = np.random.default_rng(9)
+    for a in np.concatenate([[0, m - 30_000], rng.integers(0, m - 30_000, size=40)]):
+        a = int(a)
+        b = min(a + 30_000, m)
+        lo = a + w if a > 0 else 0
+        hi = b - w if b < m else m
+        seg = keys[a:b].cpu().numpy().view(np.uint32).astype(np.uint64)
+        rh, rp = oracle.minimizers_from_keys(seg, w)
+        rp = rp.astype(np.int64) + a
+        sel = (rp >= lo) & (rp < hi)
+        i0, i1 = torch.searchsorted(pos, torch.tensor([lo, hi], device=pos.device)).tolist()
+        assert (pos[i0:i1].cpu().numpy() == rp[sel]).all() and (to_u64(h[i0:i1]) == rh[sel]).all(), a
