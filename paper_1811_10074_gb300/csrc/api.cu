@@ -231,14 +231,14 @@ sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int ki
 struct StagedWs {
   uint64_t counts_off, scan_off, tilebar_off, hash_off, pos_off, first_off, extra_off, total;
 };
-StagedWs staged_ws_layout(uint64_t tiles, int w, bool reads, uint64_t extra) {
+StagedWs staged_ws_layout(uint64_t tiles, int w, int hash_bytes, bool reads, uint64_t extra) {
   StagedWs L;
   const uint64_t slots = tiles * (uint64_t)sws::mini_fast_tile_windows(w);
   L.counts_off = 0;
   L.scan_off = round_up((tiles + 1) * 4, 256);
   L.tilebar_off = L.scan_off + round_up(sws::scan_u32_scratch_words(tiles + 1) * 4, 256);
   L.hash_off = L.tilebar_off + round_up(tiles * 8, 256);
-  L.pos_off = L.hash_off + round_up(slots * 4, 256);
+  L.pos_off = L.hash_off + round_up(slots * (uint64_t)hash_bytes, 256);
   L.first_off = L.pos_off + round_up(slots * 4, 256);
   L.extra_off = L.first_off + (reads ? round_up(slots * 4, 256) : 0);
   L.total = L.extra_off + round_up(extra, 256);
@@ -256,14 +256,15 @@ sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrie
   if (staged) {
     const uint64_t tiles = (nwin + tw - 1) / tw;
     if (tiles >= 0xffffffffull) return fail(SWS_ERR_INVALID, "input too long");
-    const StagedWs L = staged_ws_layout(tiles, a.w, barrier == sws::BAR_READS, extra);
+    const StagedWs L =
+        staged_ws_layout(tiles, a.w, sws::mini_fast_hash_bytes(source, a.k), barrier == sws::BAR_READS, extra);
     sws_status s = ensure_ws(ctx, L.total, st);
     if (s) return s;
     char *w = static_cast<char *>(ctx->ws);
     a.tile_counts = reinterpret_cast<uint32_t *>(w + L.counts_off);
     a.scan_tmp = reinterpret_cast<uint32_t *>(w + L.scan_off);
     a.tile_bar = reinterpret_cast<uint2 *>(w + L.tilebar_off);
-    a.stg_hash = reinterpret_cast<uint32_t *>(w + L.hash_off);
+    a.stg_hash = w + L.hash_off;
     a.stg_pos = reinterpret_cast<uint32_t *>(w + L.pos_off);
     a.stg_first = reinterpret_cast<uint32_t *>(w + L.first_off);
     a.err = ctx->d_err;

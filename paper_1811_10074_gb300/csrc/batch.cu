@@ -81,7 +81,7 @@ Layout layout_for(const sws_batch *b, int path) {
     L.scan = rup((L.tiles + 1) * 4, 256);
     L.tilebar = L.scan + rup(sws::scan_u32_scratch_words(L.tiles + 1) * 4, 256);
     L.shash = L.tilebar + rup(L.tiles * 8, 256);
-    L.spos = L.shash + rup(slots * 4, 256);
+    L.spos = L.shash + rup(slots * (uint64_t)sws::mini_fast_hash_bytes(sws::SRC_DNA, b->k), 256);
     L.sfirst = L.spos + rup(slots * 4, 256);
     L.fix = L.sfirst + rup(slots * 4, 256);
     L.bytes = L.fix + rup(fixb, 256);
@@ -125,7 +125,7 @@ sws_status enqueue(sws_batch *b, int path, cudaStream_t st) {
     a.tile_counts = reinterpret_cast<uint32_t *>(ws + L.counts);
     a.scan_tmp = reinterpret_cast<uint32_t *>(ws + L.scan);
     a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar);
-    a.stg_hash = reinterpret_cast<uint32_t *>(ws + L.shash);
+    a.stg_hash = ws + L.shash;
     a.stg_pos = reinterpret_cast<uint32_t *>(ws + L.spos);
     a.stg_first = reinterpret_cast<uint32_t *>(ws + L.sfirst);
     fix = reinterpret_cast<uint64_t *>(ws + L.fix);

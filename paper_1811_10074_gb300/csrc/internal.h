@@ -56,7 +56,7 @@ struct MiniArgs {
   // staged path only
   uint32_t *tile_counts;  // [num_tiles + 1], exclusive offsets after the scan
   uint32_t *scan_tmp;     // scan_u32_scratch_words(num_tiles + 1)
-  uint32_t *stg_hash;     // [num_tiles * windows per tile]
+  void *stg_hash;         // [num_tiles * windows per tile] values, mini_fast_hash_bytes each
   uint32_t *stg_pos;
   uint32_t *stg_first;    // read batches: read index of a read's first pick, else ~0
   // When set, the sizes (n, nbar, windows, tiles) are read from this device descriptor at run
@@ -80,6 +80,7 @@ cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrie
 // Staged path (w in 4..16, keys of at most 32 bits): a persistent kernel writes each tile's picks
 // to a fixed slot, a scan of the per-tile counts gives offsets, a gather puts picks in order.
 bool mini_fast_applies(int source, int k, int w);
+int mini_fast_hash_bytes(int source, int k);  // bytes of a staged key value: 8 when 2k > 32
 int mini_fast_tile_windows(int w);
 cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
                                      cudaStream_t stream);

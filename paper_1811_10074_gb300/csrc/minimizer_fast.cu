@@ -1,6 +1,5 @@
-// minimizer_fast.cu -- minimizers for window lengths w = 4..16 with keys of at most 32 bits
-// (k <= 16, or precomputed 32-bit keys), in three steps that never wait on one another inside a
-// kernel:
+// minimizer_fast.cu -- minimizers for window lengths w = 4..16 (any k <= 32, or precomputed
+// 32-bit keys), in three steps that never wait on one another inside a kernel:
 //
 //   1. k_mini_stage (persistent, one CTA per resident slot, tiles assigned statically): keys of a
 //      tile's k-mers, the least key of every window (Sec. 2.4) by block-combine, which windows
@@ -17,7 +16,7 @@
 // * A tile starts at a multiple of w and a thread owns VPT = w * floor(16 / w) consecutive k-mers,
 //   so the blocks of w are whole, compile-time groups of registers: the block-combine (in-block
 //   suffix minimum with the next block's prefix minimum) needs no segment bookkeeping and runs on
-//   32-bit values, one min per step.
+//   the key values themselves (32-bit for 2k <= 32 and precomputed keys, 64-bit otherwise).
 // * Ties.  Keys are ordered by (value, position).  Instead of 64-bit keys, the scans carry a 32-bit
 //   value and the position of its leftmost occurrence: a prefix step takes the new element only
 //   when strictly smaller, a suffix step when smaller or equal, and a window's suffix part (left)
@@ -40,7 +39,7 @@ constexpr int FNT = 256;
 constexpr int FNW = FNT / 32;
 constexpr int FMAXB = 128;
 
-template <int W, int SRC, int BAR>
+template <int W, int SRC, int BAR, class V>
 struct Geo {
   static constexpr int NB = 16 / W;              // blocks of w per thread
   static constexpr int VPT = W * NB;             // k-mers per thread
@@ -48,10 +47,10 @@ struct Geo {
   static constexpr int TW = (FNT * NB - 2) * W;  // windows per tile (a multiple of w)
   static constexpr int STAGE = SRC == SRC_DNA ? ((63 + L + 16) / 4 + 16 + 15) / 16 * 16 : (L + 8) * 4;
   static constexpr int OFF_SX = 2 * STAGE;  // DNA: keys of the tile, sx[o + 1] (keys: read from the stage)
-  static constexpr int OFF_BAR = OFF_SX + (SRC == SRC_DNA ? ((L + 2) * 4 + 15) / 16 * 16 : 0);
+  static constexpr int OFF_BAR = OFF_SX + (SRC == SRC_DNA ? ((L + 2) * (int)sizeof(V) + 15) / 16 * 16 : 0);
   static constexpr int OFF_PICKS = OFF_BAR + FMAXB * 16;
-  static constexpr int PICK_WORDS = BAR == BAR_READS ? 3 : 2;
-  static constexpr int BYTES = OFF_PICKS + TW * 4 * PICK_WORDS;
+  // picks: value (V), position, and for read batches the read index of a read's first pick
+  static constexpr int BYTES = OFF_PICKS + TW * ((int)sizeof(V) + (BAR == BAR_READS ? 8 : 4));
 };
 
 __device__ __forceinline__ long long floor_div(long long a, long long b) {
@@ -64,16 +63,17 @@ struct Staging {
   long long bulk;  // bytes of the bulk copy (0: none)
 };
 
-template <int W, int BAR, int SRC>
+template <int W, int BAR, int SRC, class V>
 __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, int span,
                                                     const uint2 *__restrict__ tile_bar, uint32_t num_tiles) {
-  using G = Geo<W, SRC, BAR>;
+  using G = Geo<W, SRC, BAR, V>;
+  constexpr V NONE = ~(V)0;
   constexpr int VPT = G::VPT, NB = G::NB, WM1 = W > 1 ? W - 1 : 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t *sx = reinterpret_cast<uint32_t *>(smem + G::OFF_SX);
+  V *sx = reinterpret_cast<V *>(smem + G::OFF_SX);
   long long *sbar = reinterpret_cast<long long *>(smem + G::OFF_BAR);
-  uint32_t *sh_hash = reinterpret_cast<uint32_t *>(smem + G::OFF_PICKS);
-  uint32_t *sh_pos = sh_hash + G::TW;
+  V *sh_hash = reinterpret_cast<V *>(smem + G::OFF_PICKS);
+  uint32_t *sh_pos = reinterpret_cast<uint32_t *>(sh_hash + G::TW);
   uint32_t *sh_first = sh_pos + G::TW;  // read batches only
   __shared__ unsigned long long s_mbar[2];
   __shared__ Staging s_st[2];
@@ -194,48 +194,61 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     const long long lastv = (long long)n - (SRC == SRC_DNA ? a.k : 1);  // last valid k-mer
     const int jlo = interior ? 0 : (ifirst < 0 ? (int)(-ifirst < VPT ? -ifirst : VPT) : 0);
     const int jhi = interior ? VPT : (lastv < ifirst ? 0 : (int)(lastv - ifirst + 1 < VPT ? lastv - ifirst + 1 : VPT));
-    uint32_t x[VPT];
+    V x[VPT];
     if (SRC == SRC_DNA) {
       const uint32_t *sw = reinterpret_cast<const uint32_t *>(stage);
       const int r = (int)(i0 - 4 * stg.gb0) + t * VPT;  // staged base of this thread's first k-mer
       const int q = r >> 4, s = (r & 15) * 2;
-      const uint32_t v0 = __funnelshift_r(sw[q], sw[q + 1], s);
+      const uint32_t v0 = __funnelshift_r(sw[q], sw[q + 1], s);  // bases r .. r+15
       const uint32_t v1 = __funnelshift_r(sw[q + 1], sw[q + 2], s);
       const int k = a.k;
-      const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+      if (sizeof(V) == 4) {
+        const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) {
-        const uint32_t v = key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), a.mode, kmask);
-        x[j] = (j >= jlo && j < jhi) ? v : 0xFFFFFFFFu;
+        for (int j = 0; j < VPT; ++j) {
+          const uint32_t v = key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), a.mode, kmask);
+          x[j] = (j >= jlo && j < jhi) ? (V)v : NONE;
+        }
+      } else {
+        const uint32_t v2 = __funnelshift_r(sw[q + 2], sw[q + 3], s);
+        const unsigned long long kmask = 2 * k == 64 ? ~0ull : ((1ull << (2 * k)) - 1ull);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+          const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
+                                         __funnelshift_r(v0, v1, 2 * j);
+          const unsigned long long v = key_value64(kmer64(w64, k, kmask), a.mode, kmask);
+          x[j] = (j >= jlo && j < jhi) ? (V)v : NONE;
+        }
       }
     } else {
       const uint32_t *sk = reinterpret_cast<const uint32_t *>(stage);
       const int r = (int)(i0 - stg.gb0 / 4) + t * VPT;
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) x[j] = (j >= jlo && j < jhi) ? sk[r + j] : 0xFFFFFFFFu;
+      for (int j = 0; j < VPT; ++j) x[j] = (j >= jlo && j < jhi) ? (V)sk[r + j] : NONE;
     }
     // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
     // tile's keys go through shared memory; precomputed keys are read from the stage directly.
-    const uint32_t *kx;  // kx[o]: key of tile-local k-mer o
+    const V *kx;  // kx[o]: key of tile-local k-mer o
     if (SRC == SRC_DNA) {
 #pragma unroll
       for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
       __syncthreads();
       kx = sx + 1;
     } else {
-      kx = reinterpret_cast<const uint32_t *>(stage) + (i0 - stg.gb0 / 4);
+      kx = reinterpret_cast<const V *>(stage) + (i0 - stg.gb0 / 4);  // V is 32-bit for precomputed keys
     }
 
     // ---- window minima and their leftmost positions, by block-combine on registers -----------
     // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
     // on ties (strict <), suffix minima the earliest too (<=); a window's suffix part lies left of
     // its prefix part, so ties between the two go to the suffix.
-    uint32_t xn[WM1];  // the next thread's first w-1 keys
+    V xn[WM1];  // the next thread's first w-1 keys
 #pragma unroll
     for (int i = 0; i < W - 1; ++i) xn[i] = kx[(t + 1 < FNT ? t + 1 : t) * VPT + i];
-    const uint32_t xprev = t > 0 ? kx[t * VPT - 1] : 0xFFFFFFFFu;  // key of k-mer ifirst - 1 (unused for thread 0)
+    const V xprev = t > 0 ? kx[t * VPT - 1] : NONE;  // key of k-mer ifirst - 1 (unused for thread 0)
     const int o0 = t * VPT;
-    uint32_t P[VPT], S[VPT], Pp[VPT], Sp[VPT], Pn[WM1], Pnp[WM1], y[VPT], yp[VPT];
+    V P[VPT], S[VPT], Pn[WM1], y[VPT];
+    uint32_t Pp[VPT], Sp[VPT], Pnp[WM1], yp[VPT];
 #pragma unroll
     for (int b2 = 0; b2 < NB; ++b2) {
       P[b2 * W] = x[b2 * W];
@@ -274,7 +287,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 #pragma unroll
       for (int i = 1; i < W; ++i) {
         const int j = b2 * W + i;
-        const uint32_t pr = (b2 + 1 < NB) ? P[(b2 + 1) * W + i - 1] : Pn[i - 1];
+        const V pr = (b2 + 1 < NB) ? P[(b2 + 1) * W + i - 1] : Pn[i - 1];
         const uint32_t prp = (b2 + 1 < NB) ? Pp[(b2 + 1) * W + i - 1] : Pnp[i - 1];
         const bool c = S[j] <= pr;
         y[j] = c ? S[j] : pr;
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     __syncthreads();
     const uint64_t slot = (uint64_t)tile * G::TW;
     for (uint32_t i = t; i < total; i += FNT) {
-      a.stg_hash[slot + i] = sh_hash[i];
+      static_cast<V *>(a.stg_hash)[slot + i] = sh_hash[i];
       a.stg_pos[slot + i] = sh_pos[i];
       if (BAR == BAR_READS) a.stg_first[slot + i] = sh_first[i];
     }
@@ -388,21 +401,23 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 // requests in flight (the copy is latency bound otherwise).
 constexpr int GNT = 256, GUNROLL = 4;
 
-template <int BAR>
+template <int BAR, class V>
 __global__ void __launch_bounds__(GNT) k_mini_gather(MiniArgs a, uint32_t num_tiles, int TW) {
   if (a.desc) num_tiles = (uint32_t)a.desc[BD_TILES];
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = a.tile_counts[num_tiles];
-  uint32_t *gh = static_cast<uint32_t *>(a.hash_out);
+  V *gh = static_cast<V *>(a.hash_out);
+  const V *sh = static_cast<const V *>(a.stg_hash);
   for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
     const uint32_t o = a.tile_counts[tile], c = a.tile_counts[tile + 1] - o;
     const uint64_t slot = tile * (uint64_t)TW;
     for (uint32_t b = 0; b < c; b += GNT * GUNROLL) {
-      uint32_t h[GUNROLL], p[GUNROLL], f[GUNROLL];
+      V h[GUNROLL];
+      uint32_t p[GUNROLL], f[GUNROLL];
 #pragma unroll
       for (int u = 0; u < GUNROLL; ++u) {
         const uint32_t i = b + u * GNT + threadIdx.x;
         if (i < c) {
-          h[u] = a.stg_hash[slot + i];
+          h[u] = sh[slot + i];
           p[u] = a.stg_pos[slot + i];
           f[u] = BAR == BAR_READS ? a.stg_first[slot + i] : 0xFFFFFFFFu;
         }
@@ -423,11 +438,11 @@ __global__ void __launch_bounds__(GNT) k_mini_gather(MiniArgs a, uint32_t num_ti
   }
 }
 
-template <int W, int BAR, int SRC>
+template <int W, int BAR, int SRC, class V>
 cudaError_t launch_w(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, uint64_t nwin, int span,
                      int num_sms, cudaStream_t st) {
-  auto kern = k_mini_stage<W, BAR, SRC>;
-  const size_t sm = Geo<W, SRC, BAR>::BYTES;
+  auto kern = k_mini_stage<W, BAR, SRC, V>;
+  const size_t sm = Geo<W, SRC, BAR, V>::BYTES;
   static int per_sm = 0;  // resident CTAs per SM for this instantiation
   if (per_sm == 0) {
     if (sm > 48 * 1024) {
@@ -445,23 +460,23 @@ cudaError_t launch_w(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_ba
   return cudaGetLastError();
 }
 
-template <int BAR, int SRC>
+template <int BAR, int SRC, class V>
 cudaError_t launch_bar(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, uint64_t nwin, int span,
                        int num_sms, cudaStream_t st) {
   switch (a.w) {
-    case 4: return launch_w<4, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 5: return launch_w<5, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 6: return launch_w<6, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 7: return launch_w<7, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 8: return launch_w<8, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 9: return launch_w<9, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 10: return launch_w<10, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 11: return launch_w<11, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 12: return launch_w<12, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 13: return launch_w<13, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 14: return launch_w<14, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 15: return launch_w<15, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    case 16: return launch_w<16, BAR, SRC>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 4: return launch_w<4, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 5: return launch_w<5, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 6: return launch_w<6, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 7: return launch_w<7, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 8: return launch_w<8, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 9: return launch_w<9, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 10: return launch_w<10, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 11: return launch_w<11, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 12: return launch_w<12, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 13: return launch_w<13, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 14: return launch_w<14, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 15: return launch_w<15, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+    case 16: return launch_w<16, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
     default: return cudaErrorNotSupported;
   }
 }
@@ -469,8 +484,10 @@ cudaError_t launch_bar(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_
 }  // namespace
 
 bool mini_fast_applies(int source, int k, int w) {
-  return w >= 4 && w <= 16 && (source == SRC_KEYS || 2 * k <= 32);
+  return w >= 4 && w <= 16 && (source == SRC_KEYS || (k >= 1 && k <= 32));
 }
+
+int mini_fast_hash_bytes(int source, int k) { return source == SRC_DNA && 2 * k > 32 ? 8 : 4; }
 
 int mini_fast_tile_windows(int w) { return w >= 4 && w <= 16 ? (FNT * (16 / w) - 2) * w : 0; }
 
@@ -487,16 +504,27 @@ cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier,
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  if (source == SRC_KEYS) e = launch_bar<BAR_NBLOCK, SRC_KEYS>(a, num_tiles, nullptr, nwin, span, num_sms, st);
-  else if (barrier == BAR_READS) e = launch_bar<BAR_READS, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-  else e = launch_bar<BAR_NBLOCK, SRC_DNA>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+  const bool k64 = mini_fast_hash_bytes(source, a.k) == 8;
+  using U64 = unsigned long long;
+  if (source == SRC_KEYS) e = launch_bar<BAR_NBLOCK, SRC_KEYS, uint32_t>(a, num_tiles, nullptr, nwin, span, num_sms, st);
+  else if (barrier == BAR_READS)
+    e = k64 ? launch_bar<BAR_READS, SRC_DNA, U64>(a, num_tiles, tile_bar, nwin, span, num_sms, st)
+            : launch_bar<BAR_READS, SRC_DNA, uint32_t>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+  else
+    e = k64 ? launch_bar<BAR_NBLOCK, SRC_DNA, U64>(a, num_tiles, tile_bar, nwin, span, num_sms, st)
+            : launch_bar<BAR_NBLOCK, SRC_DNA, uint32_t>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
   if (e != cudaSuccess) return e;
   if (a.desc) e = scan_u32_dev(a.tile_counts, num_tiles + 1, a.desc + BD_SCAN_LEN, a.scan_tmp, st);
   else e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)(num_tiles < (1u << 20) ? num_tiles : (1u << 20));
-  if (barrier == BAR_READS) k_mini_gather<BAR_READS><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
-  else k_mini_gather<BAR_NBLOCK><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  if (barrier == BAR_READS) {
+    if (k64) k_mini_gather<BAR_READS, U64><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+    else k_mini_gather<BAR_READS, uint32_t><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  } else {
+    if (k64) k_mini_gather<BAR_NBLOCK, U64><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+    else k_mini_gather<BAR_NBLOCK, uint32_t><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);
+  }
   return cudaGetLastError();
 }
 

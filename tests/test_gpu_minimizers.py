@@ -143,7 +143,8 @@ def test_minimizers_batch_matches_per_read_oracle():
         assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
 
 
-# Every window length of the kernel specialized on w (4..16, keys of at most 32 bits).  The API
+# Every window length of the kernel specialized on w (4..16; 32-bit key values for 2k <= 32 and
+# 64-bit ones above).  The API
 # takes that (staged) path once an input fills the GPU, more than (256 * floor(16/w) - 2) * w
 # windows per SM; 640 tiles plus a ragged tail exceed it on a 152-SM GB300, and a 3-tile input
 # takes the single-kernel look-back path.
@@ -151,7 +152,7 @@ def test_minimizers_batch_matches_per_read_oracle():
 def test_specialized_window_lengths(w):
     rng = np.random.default_rng(1000 + w)
     tw = (256 * (16 // w) - 2) * w
-    for k, mode in ((15, "hash"), (16, "fwd"), (5, "canonical")):
+    for k, mode in ((15, "hash"), (16, "fwd"), (5, "canonical"), (19, "hash"), (32, "canonical"), (17, "fwd")):
         for ntiles in (640, 3):
             n = ntiles * tw + int(rng.integers(1, tw))
             seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
