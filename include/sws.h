@@ -72,7 +72,9 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
 #define SWS_OP_ADD_F32 5
 
 /* Algorithm variants. */
-#define SWS_VARIANT_AUTO 0          /* the library's choice (block combine, streamed when it applies) */
+#define SWS_VARIANT_AUTO 0          /* the library's choice (block combine: in registers for w <= 8,
+                                       warp-private or CTA streams on large inputs, one-shot tiles
+                                       otherwise)                                                  */
 #define SWS_VARIANT_BLOCK_COMBINE 1 /* blocks of w: in-block suffix + next-block prefix, O(1)/output;
                                        one-shot CTA tiles                                          */
 #define SWS_VARIANT_DOUBLING 2      /* ceil(log2 w) doubling levels, O(log w)/output            */
@@ -84,6 +86,11 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
                                        bytes, else SWS_ERR_UNSUPPORTED.  A copy that never completes within
                                        about a second sets the context's error word (reported by
                                        sws_sync as SWS_ERR_TIMEOUT).                               */
+#define SWS_VARIANT_BLOCK_COMBINE_WARP 5 /* block combine in warp-private streams (each warp walks its
+                                       own run of 2 KB tiles fed by 2-D TMA copies; no CTA barrier,
+                                       no halo); needs w = c*G with c = 16 (int32/fp32) or 8 (affine)
+                                       and G in {1,2,4,8,16,32}, and the input as for _STREAM, else
+                                       SWS_ERR_UNSUPPORTED.  Time-outs as for _STREAM.              */
 
 /* Failure detection self-test (no counterpart in the paper).  Queues one warp that runs one of
  * the library's bounded device-side waits against a flag that nothing ever sets:

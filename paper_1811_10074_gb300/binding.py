@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 OPS = {"add_i32": 0, "min_i32": 1, "max_i32": 2, "xor_i32": 3, "affine_u32": 4, "add_f32": 5}
-VARIANTS = {"auto": 0, "block_combine": 1, "doubling": 2, "prefix_diff": 3, "stream": 4}
+VARIANTS = {"auto": 0, "block_combine": 1, "doubling": 2, "prefix_diff": 3, "stream": 4, "warp": 5}
 KMER_KINDS = {"fwd": 0, "rc": 1, "canonical": 2, "hash": 3}
 MINI_MODES = {"hash": 0, "canonical": 1, "fwd": 2}
 

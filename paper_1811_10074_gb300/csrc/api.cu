@@ -180,7 +180,7 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   if (s) return s;
   if (op < SWS_OP_ADD_I32 || op > SWS_OP_ADD_F32) return fail(SWS_ERR_INVALID, "unknown operator %d", op);
   if (w < 1) return fail(SWS_ERR_INVALID, "w must be >= 1 (got %d)", w);
-  if (variant < SWS_VARIANT_AUTO || variant > SWS_VARIANT_BLOCK_COMBINE_STREAM)
+  if (variant < SWS_VARIANT_AUTO || variant > SWS_VARIANT_BLOCK_COMBINE_WARP)
     return fail(SWS_ERR_INVALID, "unknown variant %d", variant);
   if (n < (uint64_t)w) return SWS_OK;
   if (!in || !out) return fail(SWS_ERR_INVALID, "in/out is NULL");
@@ -205,7 +205,8 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   if (sws::slide_tile_outputs(L.cfg, es, w) == 0)
     return fail(SWS_ERR_UNSUPPORTED, "w = %d is larger than the tile of this build", w);
   cudaError_t e = sws::launch_sliding_sum(L, in, out, n, w, static_cast<cudaStream_t>(stream));
-  if (e == cudaErrorNotSupported && variant == SWS_VARIANT_BLOCK_COMBINE_STREAM)
+  if (e == cudaErrorNotSupported &&
+      (variant == SWS_VARIANT_BLOCK_COMBINE_STREAM || variant == SWS_VARIANT_BLOCK_COMBINE_WARP))
     return fail(SWS_ERR_UNSUPPORTED, "the streamed block combine does not apply to w = %d, n = %llu at this alignment",
                 w, (unsigned long long)n);
   if (e != cudaSuccess) return cuda_fail(e, "sliding-sum launch");

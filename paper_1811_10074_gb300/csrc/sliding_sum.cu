@@ -371,6 +371,146 @@ __global__ void __launch_bounds__(NT, MINB)
 }
 
 // ------------------------------------------------------------------------------------------
+// Block-combine, w = VPT * G with G a power of two <= 32: warp-private streaming (no barriers)
+// ------------------------------------------------------------------------------------------
+// Each warp owns a contiguous run of warp-tiles (32 lanes x VPT elements, 2 KB) and walks it in
+// order; its own ring of shared-memory stages is filled by 2-D TMA copies (128-byte swizzle, so
+// the lane reads are conflict free) that one lane issues ahead, on the warp's own mbarriers.
+// Blocks of w are G lanes, aligned in the warp.  Lane l needs the prefix sums of the lane G
+// later: one shuffle per element.  For lanes l < 32 - G that lane is in the same warp-tile; for
+// the others it wraps to the first block of the next warp-tile, so those lanes keep their suffix
+// sums for one iteration and emit the previous warp-tile's outputs with the next one's prefixes.
+// No CTA barrier, no shared-memory exchange, and no halo: each input is read once (plus one
+// warp-tile at the end of each warp's run).  Bounded waits as in k_slide_tma.
+template <class Op, int VPT, int NWARP, int SW, int NSTAGE>
+__global__ void __launch_bounds__(NWARP * 32)
+    k_slide_warp(const __grid_constant__ CUtensorMap tmap, const typename Op::T *__restrict__ in,
+                 typename Op::T *__restrict__ out, uint64_t n, uint64_t n_full, int w, uint64_t nwt,
+                 uint64_t per_warp, int *err) {
+  using T = typename Op::T;
+  constexpr int EPV = 16 / (int)sizeof(T);
+  constexpr int UPR = VPT / EPV;                     // 16-byte units per lane chunk
+  constexpr int WT = 32 * VPT;                       // elements per warp-tile
+  constexpr int WT_BYTES = WT * (int)sizeof(T);      // 2 KB
+  constexpr int STAGE_BYTES = SW * WT_BYTES;
+  static_assert(VPT * (int)sizeof(T) * 2 == kStreamRowBytes, "a lane chunk is half a 128-byte row");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[NWARP][NSTAGE];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char *ring = smem_raw + ((1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u) +
+                        (size_t)warp * NSTAGE * STAGE_BYTES;
+  const int G = w / VPT;
+  const int pos = lane & (G - 1);
+  const bool head = pos == 0, tail = pos == G - 1, late = lane >= 32 - G;
+  const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
+  const uint64_t k0 = gw * per_warp;
+  if (lane == 0) {
+    for (int s = 0; s < NSTAGE; ++s) tma::mbar_init(&bars[warp][s], 1);
+    tma::fence_mbar_init();
+  }
+  __syncwarp();
+  if (k0 >= nwt) return;
+  const uint64_t k1 = k0 + per_warp < nwt ? k0 + per_warp : nwt;  // this warp's outputs: warp-tiles [k0, k1)
+  const uint64_t kend = k1 < nwt ? k1 + 1 : k1;                    // plus the next one's prefixes
+  const uint64_t nstages = (kend - k0 + SW - 1) / SW;
+  auto issue = [&](uint64_t st) {  // lane 0: stage st of this warp's run into its ring slot
+    unsigned long long *bar = &bars[warp][st % NSTAGE];
+    tma::mbar_arrive_expect_tx(bar, STAGE_BYTES);
+    tma::tensor_g2s_2d(ring + (st % NSTAGE) * STAGE_BYTES, &tmap, 0, (int)((k0 + st * SW) * (WT_BYTES / kStreamRowBytes)),
+                       bar);
+  };
+  if (lane == 0) {
+    tma::prefetch_tensormap(&tmap);
+    for (uint64_t st = 0; st < (uint64_t)NSTAGE && st < nstages; ++st) issue(st);
+  }
+  const bool vec = aligned16(out);
+  const uint64_t nout = n - (uint64_t)w + 1;
+  T Sprev[VPT];
+#pragma unroll
+  for (int j = 0; j < VPT; ++j) Sprev[j] = Op::identity();
+  for (uint64_t kk = k0; kk < kend; ++kk) {
+    const uint64_t st = (kk - k0) / SW;
+    const int sub = (int)((kk - k0) % SW);
+    const int slot = (int)(st % NSTAGE);
+    if (sub == 0) {
+      const bool ok = stream_wait(&bars[warp][slot], (uint32_t)(st / NSTAGE) & 1u);
+      if (!__all_sync(kFull, ok)) {
+        if (lane == 0) {
+          atomicOr(err, DEVERR_COPY_TIMEOUT);
+          for (uint64_t s2 = st; s2 < st + NSTAGE && s2 < nstages; ++s2)
+            stream_wait(&bars[warp][s2 % NSTAGE], (uint32_t)(s2 / NSTAGE) & 1u);
+        }
+        return;
+      }
+    }
+    // this lane's VPT elements: row sub*16 + lane/2 of the stage, units 4(lane&1) .. +3, swizzled
+    T x[VPT];
+    {
+      const int row = sub * (WT_BYTES / kStreamRowBytes) + (lane >> 1);
+      const unsigned char *src = ring + slot * STAGE_BYTES + row * kStreamRowBytes;
+      uint4 u[UPR];
+#pragma unroll
+      for (int c = 0; c < UPR; ++c) u[c] = *reinterpret_cast<const uint4 *>(src + ((((lane & 1) * UPR + c) ^ (row & 7)) << 4));
+      memcpy(x, u, sizeof(u));
+    }
+    const uint64_t g = kk * (uint64_t)WT + (uint64_t)lane * VPT;
+    if (g + VPT > n_full) {
+#pragma unroll
+      for (int j = 0; j < VPT; ++j)
+        if (g + j >= n_full) x[j] = (g + j < n) ? in[g + j] : Op::identity();
+    }
+    if (sub == SW - 1 || kk + 1 == kend) {  // the stage is consumed: refill its slot
+      __syncwarp();
+      if (lane == 0 && st + NSTAGE < nstages) {
+        tma::fence_proxy_async_smem();
+        issue(st + NSTAGE);
+      }
+    }
+    T P[VPT], S[VPT];
+    P[0] = x[0];
+#pragma unroll
+    for (int j = 1; j < VPT; ++j) P[j] = Op::op(P[j - 1], x[j]);
+    S[VPT - 1] = x[VPT - 1];
+#pragma unroll
+    for (int j = VPT - 2; j >= 0; --j) S[j] = Op::op(x[j], S[j + 1]);
+    {
+      T vf = P[VPT - 1], vb = S[0];
+      for (int d = 1; d < G; d <<= 1) {
+        const T a = shfl_up_t(vf, d);
+        const T b = shfl_down_t(vb, d);
+        if (pos >= d) vf = Op::op(a, vf);
+        if (pos + d < G) vb = Op::op(vb, b);
+      }
+      const T cP = shfl_up_t(vf, 1);
+      const T cS = shfl_down_t(vb, 1);
+      if (!head) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) P[j] = Op::op(cP, P[j]);
+      }
+      if (!tail) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) S[j] = Op::op(S[j], cS);
+      }
+    }
+    // outputs: this warp-tile's (early lanes) or the previous one's (late lanes)
+    const int src_lane = (lane + G) & 31;
+    const T plast = shfl_idx_t(P[VPT - 1], (lane + G - 1) & 31);
+    T y[VPT];
+    y[0] = head ? (late ? Sprev[0] : S[0]) : Op::op(late ? Sprev[0] : S[0], plast);
+#pragma unroll
+    for (int j = 1; j < VPT; ++j) y[j] = Op::op(late ? Sprev[j] : S[j], shfl_idx_t(P[j - 1], src_lane));
+    const bool mine = late ? (kk > k0) : (kk < k1);
+    if (mine) {
+      const uint64_t go = late ? g - (uint64_t)WT : g;
+      store_tile<Op, VPT>(out, nout, go, 0, 0x7fffffff, vec, y);
+    }
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) Sprev[j] = S[j];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Block-combine for w in {1, 2, 4, 8} dividing VPT: everything in registers
 // ------------------------------------------------------------------------------------------
 // Each thread owns VPT consecutive outputs starting at a multiple of VPT (hence of W) and loads
@@ -678,6 +818,71 @@ cudaError_t launch_stream(const void *in, void *out, uint64_t n, int w, int num_
   return cudaGetLastError();
 }
 
+// Warp-private streaming block-combine: w = VPT * G, G a power of two <= 32.  The run shape
+// (warps per CTA, warp-tiles per stage, stages) is chosen by G: narrow blocks want more bytes in
+// flight per warp, wide blocks more warps (measured on GB300 over the sweep's operators).
+template <class Op, int NWARP, int SW, int NSTAGE>
+cudaError_t launch_warp_shape(const CUtensorMap &map, const void *in, void *out, uint64_t n, uint64_t n_full, int w,
+                              uint64_t nwt, int num_sms, int *err, cudaStream_t st) {
+  using T = typename Op::T;
+  constexpr int VPT = kStreamRowBytes / 2 / (int)sizeof(T);
+  constexpr int STAGE_BYTES = SW * 32 * VPT * (int)sizeof(T);
+  const size_t smem = (size_t)NWARP * NSTAGE * STAGE_BYTES + 1024;
+  auto kern = k_slide_warp<Op, VPT, NWARP, SW, NSTAGE>;
+  static int per_sm[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
+  if (nb == 0) {
+    e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NWARP * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) per_sm[dev] = nb;
+  }
+  const uint64_t warps = (uint64_t)num_sms * nb * NWARP;
+  const uint64_t per_warp = (nwt + warps - 1) / warps;
+  const uint64_t grid = ((nwt + per_warp - 1) / per_warp + NWARP - 1) / NWARP;
+  kern<<<(unsigned)grid, NWARP * 32, smem, st>>>(map, static_cast<const T *>(in), static_cast<T *>(out), n, n_full, w,
+                                                 nwt, per_warp, err);
+  return cudaGetLastError();
+}
+
+template <class Op>
+cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int num_sms, int *err, cudaStream_t st,
+                               bool quiet_unsupported) {
+  using T = typename Op::T;
+  constexpr int ES = (int)sizeof(T);
+  constexpr int VPT = kStreamRowBytes / 2 / ES;  // 16 for 4-byte elements, 8 for affine pairs
+  constexpr int WT = 32 * VPT;
+  const int G = w % VPT == 0 ? w / VPT : 0;
+  const uint64_t rows = n * ES / kStreamRowBytes;
+  EncodeTiled enc = encode_tiled();
+  if (G < 1 || G > 32 || (G & (G - 1)) != 0 || rows == 0 || rows > (1ull << 32) ||
+      (reinterpret_cast<uintptr_t>(in) & 15u) != 0 || !enc || num_sms < 1 || err == nullptr)
+    return quiet_unsupported ? cudaErrorNotSupported : cudaErrorInvalidValue;
+  // one warp-tile past the last full one: the lanes that emit a tile late need the next tile's
+  // prefixes even when n is a multiple of the warp-tile (that tile is then all identity)
+  const uint64_t nwt = n / WT + 1;
+  if (nwt * (uint64_t)(WT * ES / kStreamRowBytes) > 0x7fffffffull) return cudaErrorNotSupported;
+  const int sw = G == 1 ? 8 : (G <= 4 ? 4 : 2);  // warp-tiles per stage of the shape below
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {kStreamRowBytes / 4, rows};
+  const cuuint64_t gstride[1] = {kStreamRowBytes};
+  const cuuint32_t box[2] = {kStreamRowBytes / 4, (cuuint32_t)(sw * WT * ES / kStreamRowBytes)};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(in), gdim, gstride, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const uint64_t n_full = rows * kStreamRowBytes / ES;
+  if (G == 1) return launch_warp_shape<Op, 4, 8, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
+  if (G <= 4) return launch_warp_shape<Op, 8, 4, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
+  return launch_warp_shape<Op, 16, 2, 3>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
+}
+
 template <class Op, class Cfg>
 cudaError_t launch_op(const SlideLaunch &SL, const void *in, void *out, uint64_t n, int w, cudaStream_t st) {
   using T = typename Op::T;
@@ -686,7 +891,14 @@ cudaError_t launch_op(const SlideLaunch &SL, const void *in, void *out, uint64_t
   const int variant = SL.variant;
   if (variant == SWS_VARIANT_BLOCK_COMBINE_STREAM)
     return launch_stream<Op, S::NT, S::VPT, MINB>(in, out, n, w, SL.num_sms, SL.err, st, true);
+  if (variant == SWS_VARIANT_BLOCK_COMBINE_WARP) return launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true);
   if (variant == SWS_VARIANT_AUTO && !(w <= 8 && S::VPT % w == 0)) {
+    // warp-private streaming when w's blocks fit a warp and the input fills the GPU a few times
+    constexpr uint64_t WT = 32 * (kStreamRowBytes / 2 / sizeof(T));
+    if (n / WT >= 64ull * (uint64_t)SL.num_sms) {
+      const cudaError_t e = launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true);
+      if (e != cudaErrorNotSupported) return e;
+    }
     // streamed when the grid fills the GPU at least twice; the one-shot tiles otherwise
     const int TOs = stream_tile_outputs(S::L, (int)sizeof(T), w);
     if (TOs > 0 && (n - (uint64_t)w + 1) / (uint64_t)TOs >= 2ull * (uint64_t)SL.num_sms * (uint64_t)MINB) {

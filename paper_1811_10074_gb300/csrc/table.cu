@@ -90,10 +90,10 @@ __global__ void __launch_bounds__(RNT) k_radix_hist(PassIn in, uint64_t m, int s
 #pragma unroll 4
   for (int j = 0; j < RKPT; ++j) {
     const uint64_t i = base + (uint64_t)j * RNT + t;
-    if (i < m) {
-      unsigned long long key;
-      uint32_t val = 0;
-      fetch<WIDE>(in, i, key, val);
+    if (i < m) {  // the digit needs the key only (not the position of a wide key)
+      const unsigned long long key = in.keys ? in.keys[i]
+                                     : WIDE ? in.hash64[i]
+                                            : (unsigned long long)in.hash32[i] << 32;
       atomicAdd(&h[digit_of(key, shift)], 1u);
     }
   }

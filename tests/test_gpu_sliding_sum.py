@@ -133,3 +133,50 @@ def test_stream_variant_unsupported_shapes(op):
     y = B.sliding_sum(op, 4 * c, x[1:])
     torch.cuda.synchronize()
     assert_sampled(op, 4 * c, x[1:], y, sample_indices(y.shape[0], np.random.default_rng(1)))
+
+
+# ---------------------------------------------------------------------------------------------
+# the warp-private streaming block combine ("warp"): blocks of G = 1..32 lanes
+# ---------------------------------------------------------------------------------------------
+def warp_ws(op):
+    c = 8 if op == "affine_u32" else 16
+    return [c, 2 * c, 4 * c, 8 * c, 16 * c, 32 * c]
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_warp_variant_matches_oracle(op):
+    """Runs shorter and longer than one warp's share, ragged tails inside a 128-byte row."""
+    es = 8 if op == "affine_u32" else 4
+    for w in warp_ws(op):
+        for n in (w, w + 40, 2048 + 7, 3 * 8192 + 17, 100_003):
+            x, ref = oracle_sliding(op, w, n, 13, op in INT_OPS)
+            if n * es < 128:  # less than one 128-byte row: not for the tensor copies
+                with pytest.raises(B.SwsError, match="UNSUPPORTED"):
+                    B.sliding_sum(op, w, x.cuda(), variant="warp")
+                continue
+            y = B.sliding_sum(op, w, x.cuda(), variant="warp")
+            torch.cuda.synchronize()
+            assert_sliding_equal(op, w, x, y, ref)
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_warp_variant_many_tiles_per_warp(op):
+    """Long runs per warp (stage slots and mbarrier phases wrap many times), against the one-shot
+    kernel bit for bit and the oracle on sampled outputs."""
+    rng = np.random.default_rng(4)
+    n = (1 << 23) + 29
+    x = make_input(op, n, seed=6, device="cuda")
+    for w in warp_ws(op):
+        y = B.sliding_sum(op, w, x, variant="warp")
+        yb = B.sliding_sum(op, w, x, variant="block_combine")
+        torch.cuda.synchronize()
+        if op != "add_f32":
+            assert torch.equal(y, yb), (op, w)
+        assert_sampled(op, w, x, y, sample_indices(n - w + 1, rng, 4096))
+
+
+def test_warp_variant_unsupported_shapes():
+    x = make_input("add_i32", 1 << 20, device="cuda")
+    for w, xv in ((48, x), (1024, x), (64, x[1:]), (16, x[:20])):
+        with pytest.raises(B.SwsError, match="UNSUPPORTED"):
+            B.sliding_sum("add_i32", w, xv, variant="warp")
