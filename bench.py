@@ -291,7 +291,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n": n, "ops": args.ops, "w": args.ws, "calls_per_step": len(cases),
                    "bytes_per_step": step_bytes, "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "sliding-sum block combine (k_slide_small for w=4, k_slide_tma otherwise)",
+        "roofline": {"kernel": "sliding-sum block combine (k_slide_small for w=4, warp-private k_slide_warp / k_slide_wblk otherwise)",
                      "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,

@@ -511,6 +511,143 @@ __global__ void __launch_bounds__(NWARP * 32)
 }
 
 // ------------------------------------------------------------------------------------------
+// Block-combine, w = 32 * M * VPT (blocks of M whole warp-tiles): warp-private streaming
+// ------------------------------------------------------------------------------------------
+// Each warp walks its run of blocks with each block one stage of its shared-memory ring (2-D TMA,
+// 128-byte swizzle).  Outputs of block b need block b's suffix sums and block b+1's prefix sums
+// at the same offset, which belong to the same lane: the warp keeps blocks b and b+1 resident and,
+// warp-tile by warp-tile, scans b+1 forward (carrying the running total of its earlier warp-
+// tiles) and b backward (carrying the totals of its later warp-tiles, known from when b was the
+// next block), combining as it goes.  No CTA barrier, no halo: each input is read from HBM once.
+template <class Op, int VPT, int M, int NWARP, int NSTAGE>
+__global__ void __launch_bounds__(NWARP * 32)
+    k_slide_wblk(const __grid_constant__ CUtensorMap tmap, const typename Op::T *__restrict__ in,
+                 typename Op::T *__restrict__ out, uint64_t n, uint64_t n_full, uint64_t nob, uint64_t per_warp,
+                 int *err) {
+  using T = typename Op::T;
+  constexpr int EPV = 16 / (int)sizeof(T);
+  constexpr int UPR = VPT / EPV;
+  constexpr int WT = 32 * VPT;
+  constexpr int WT_BYTES = WT * (int)sizeof(T);
+  constexpr int BLK = M * WT;                  // w
+  constexpr int STAGE_BYTES = M * WT_BYTES;    // one block
+  static_assert(VPT * (int)sizeof(T) * 2 == kStreamRowBytes, "a lane chunk is half a 128-byte row");
+  static_assert(NSTAGE >= 3, "blocks b and b+1 stay resident while b+2 loads");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[NWARP][NSTAGE];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char *ring = smem_raw + ((1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u) +
+                        (size_t)warp * NSTAGE * STAGE_BYTES;
+  const uint64_t gw = (uint64_t)blockIdx.x * NWARP + warp;
+  const uint64_t b0 = gw * per_warp;
+  if (lane == 0) {
+    for (int s = 0; s < NSTAGE; ++s) tma::mbar_init(&bars[warp][s], 1);
+    tma::fence_mbar_init();
+  }
+  __syncwarp();
+  if (b0 >= nob) return;
+  const uint64_t b1 = b0 + per_warp < nob ? b0 + per_warp : nob;  // output blocks [b0, b1)
+  const uint64_t nst = b1 - b0 + 1;                                  // input blocks b0 .. b1
+  auto issue = [&](uint64_t s) {
+    unsigned long long *bar = &bars[warp][s % NSTAGE];
+    tma::mbar_arrive_expect_tx(bar, STAGE_BYTES);
+    tma::tensor_g2s_2d(ring + (s % NSTAGE) * STAGE_BYTES, &tmap, 0, (int)((b0 + s) * (STAGE_BYTES / kStreamRowBytes)),
+                       bar);
+  };
+  if (lane == 0) {
+    tma::prefetch_tensormap(&tmap);
+    for (uint64_t s = 0; s < (uint64_t)NSTAGE && s < nst; ++s) issue(s);
+  }
+  // lane chunk j of the block in stage s (global block b), patched past the tensor's full rows
+  auto load_chunk = [&](uint64_t s, uint64_t b, int j, T (&x)[VPT]) {
+    const int row = j * (WT_BYTES / kStreamRowBytes) + (lane >> 1);
+    const unsigned char *src = ring + (s % NSTAGE) * STAGE_BYTES + row * kStreamRowBytes;
+    uint4 u[UPR];
+#pragma unroll
+    for (int c = 0; c < UPR; ++c) u[c] = *reinterpret_cast<const uint4 *>(src + ((((lane & 1) * UPR + c) ^ (row & 7)) << 4));
+    memcpy(x, u, sizeof(u));
+    const uint64_t g = b * (uint64_t)BLK + (uint64_t)j * WT + (uint64_t)lane * VPT;
+    if (g + VPT > n_full) {
+#pragma unroll
+      for (int i = 0; i < VPT; ++i)
+        if (g + i >= n_full) x[i] = (g + i < n) ? in[g + i] : Op::identity();
+    }
+  };
+  const bool vec = aligned16(out);
+  const uint64_t nout = n - (uint64_t)BLK + 1;
+  T tot[M];  // warp-tile totals of the block that is "next" (becomes "current" one step later)
+  for (uint64_t s = 0; s < nst; ++s) {
+    const uint64_t b = b0 + s;  // the block in stage s: "next"; block b-1 is "current"
+    const bool ok = stream_wait(&bars[warp][s % NSTAGE], (uint32_t)(s / NSTAGE) & 1u);
+    if (!__all_sync(kFull, ok)) {
+      if (lane == 0) {
+        atomicOr(err, DEVERR_COPY_TIMEOUT);
+        for (uint64_t s2 = s; s2 < s + NSTAGE && s2 < nst; ++s2)
+          stream_wait(&bars[warp][s2 % NSTAGE], (uint32_t)(s2 / NSTAGE) & 1u);
+      }
+      return;
+    }
+    // suffix carries of the current block: sufT[j] = tot[j] (+) ... (+) tot[M-1]
+    T sufT[M + 1];
+    sufT[M] = Op::identity();
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) sufT[j] = (s > 0) ? Op::op(tot[j], sufT[j + 1]) : Op::identity();
+    T carryP = Op::identity();  // prefix of the next block up to the end of the previous warp-tile
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      // next block, warp-tile j: prefix sums from the block start
+      T P[VPT];
+      load_chunk(s, b, j, P);
+#pragma unroll
+      for (int i = 1; i < VPT; ++i) P[i] = Op::op(P[i - 1], P[i]);
+      T v = P[VPT - 1];
+      for (int d = 1; d < 32; d <<= 1) {
+        const T a = shfl_up_t(v, d);
+        if (lane >= d) v = Op::op(a, v);
+      }
+      const T wtot = shfl_idx_t(v, 31);
+      T ex = shfl_up_t(v, 1);
+      ex = lane == 0 ? carryP : Op::op(carryP, ex);
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) P[i] = Op::op(ex, P[i]);
+      if (s > 0) {
+        // current block, warp-tile j: suffix sums to the block end
+        T S[VPT];
+        load_chunk(s - 1, b - 1, j, S);
+#pragma unroll
+        for (int i = VPT - 2; i >= 0; --i) S[i] = Op::op(S[i], S[i + 1]);
+        T u = S[0];
+        for (int d = 1; d < 32; d <<= 1) {
+          const T a = shfl_down_t(u, d);
+          if (lane + d < 32) u = Op::op(u, a);
+        }
+        T es = shfl_down_t(u, 1);
+        es = lane == 31 ? sufT[j + 1] : Op::op(es, sufT[j + 1]);
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) S[i] = Op::op(S[i], es);
+        // y = S (current) (+) P (next) at the previous element
+        const T pprev = shfl_up_t(P[VPT - 1], 1);
+        T y[VPT];
+        y[0] = (lane == 0 && j == 0) ? S[0] : Op::op(S[0], lane == 0 ? carryP : pprev);
+#pragma unroll
+        for (int i = 1; i < VPT; ++i) y[i] = Op::op(S[i], P[i - 1]);
+        const uint64_t go = (b - 1) * (uint64_t)BLK + (uint64_t)j * WT + (uint64_t)lane * VPT;
+        store_tile<Op, VPT>(out, nout, go, 0, 0x7fffffff, vec, y);
+      }
+      carryP = Op::op(carryP, wtot);
+      tot[j] = wtot;
+    }
+    // stage s-1 (the current block) is consumed: refill its slot
+    __syncwarp();
+    if (lane == 0 && s >= 1 && s - 1 + NSTAGE < nst) {
+      tma::fence_proxy_async_smem();
+      issue(s - 1 + NSTAGE);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Block-combine for w in {1, 2, 4, 8} dividing VPT: everything in registers
 // ------------------------------------------------------------------------------------------
 // Each thread owns VPT consecutive outputs starting at a multiple of VPT (hence of W) and loads
@@ -850,6 +987,52 @@ cudaError_t launch_warp_shape(const CUtensorMap &map, const void *in, void *out,
   return cudaGetLastError();
 }
 
+template <class Op, int M, int NWARP, int NSTAGE>
+cudaError_t launch_wblk_shape(const void *in, void *out, uint64_t n, int num_sms, int *err, cudaStream_t st) {
+  using T = typename Op::T;
+  constexpr int ES = (int)sizeof(T);
+  constexpr int VPT = kStreamRowBytes / 2 / ES;
+  constexpr int BLK = M * 32 * VPT;
+  constexpr int STAGE_BYTES = BLK * ES;
+  static_assert(STAGE_BYTES / kStreamRowBytes <= 256, "a TMA box has at most 256 rows");
+  const uint64_t rows = n * ES / kStreamRowBytes;
+  const uint64_t nout = n - (uint64_t)BLK + 1;
+  const uint64_t nob = (nout + BLK - 1) / BLK;  // output blocks; input blocks 0 .. nob
+  if ((nob + 1) * (uint64_t)(STAGE_BYTES / kStreamRowBytes) > 0x7fffffffull) return cudaErrorNotSupported;
+  EncodeTiled enc = encode_tiled();
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {kStreamRowBytes / 4, rows};
+  const cuuint64_t gstride[1] = {kStreamRowBytes};
+  const cuuint32_t box[2] = {kStreamRowBytes / 4, (cuuint32_t)(STAGE_BYTES / kStreamRowBytes)};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(in), gdim, gstride, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)NWARP * NSTAGE * STAGE_BYTES + 1024;
+  auto kern = k_slide_wblk<Op, VPT, M, NWARP, NSTAGE>;
+  static int per_sm[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
+  if (nb == 0) {
+    e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NWARP * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) per_sm[dev] = nb;
+  }
+  const uint64_t warps = (uint64_t)num_sms * nb * NWARP;
+  const uint64_t per_warp = (nob + warps - 1) / warps;
+  const uint64_t grid = ((nob + per_warp - 1) / per_warp + NWARP - 1) / NWARP;
+  const uint64_t n_full = rows * kStreamRowBytes / ES;
+  kern<<<(unsigned)grid, NWARP * 32, smem, st>>>(map, static_cast<const T *>(in), static_cast<T *>(out), n, n_full, nob,
+                                                 per_warp, err);
+  return cudaGetLastError();
+}
+
 template <class Op>
 cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int num_sms, int *err, cudaStream_t st,
                                bool quiet_unsupported) {
@@ -860,9 +1043,15 @@ cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int
   const int G = w % VPT == 0 ? w / VPT : 0;
   const uint64_t rows = n * ES / kStreamRowBytes;
   EncodeTiled enc = encode_tiled();
-  if (G < 1 || G > 32 || (G & (G - 1)) != 0 || rows == 0 || rows > (1ull << 32) ||
+  const bool blocks_of_tiles = G == 64 || G == 128 || G == 256;
+  if (G < 1 || G > 256 || (G & (G - 1)) != 0 || rows == 0 || rows > (1ull << 32) ||
       (reinterpret_cast<uintptr_t>(in) & 15u) != 0 || !enc || num_sms < 1 || err == nullptr)
     return quiet_unsupported ? cudaErrorNotSupported : cudaErrorInvalidValue;
+  if (blocks_of_tiles) {  // blocks of 2, 4 or 8 whole warp-tiles
+    if (G == 64) return launch_wblk_shape<Op, 2, 16, 3>(in, out, n, num_sms, err, st);
+    if (G == 128) return launch_wblk_shape<Op, 4, 8, 3>(in, out, n, num_sms, err, st);
+    return launch_wblk_shape<Op, 8, 4, 3>(in, out, n, num_sms, err, st);
+  }
   // one warp-tile past the last full one: the lanes that emit a tile late need the next tile's
   // prefixes even when n is a multiple of the warp-tile (that tile is then all identity)
   const uint64_t nwt = n / WT + 1;

@@ -139,8 +139,9 @@ def test_stream_variant_unsupported_shapes(op):
 # the warp-private streaming block combine ("warp"): blocks of G = 1..32 lanes
 # ---------------------------------------------------------------------------------------------
 def warp_ws(op):
+    """Blocks of 1..32 lanes, and blocks of 2, 4 and 8 whole warp-tiles."""
     c = 8 if op == "affine_u32" else 16
-    return [c, 2 * c, 4 * c, 8 * c, 16 * c, 32 * c]
+    return [c, 2 * c, 4 * c, 8 * c, 16 * c, 32 * c, 64 * c, 128 * c, 256 * c]
 
 
 @pytest.mark.parametrize("op", OPS)
@@ -148,7 +149,7 @@ def test_warp_variant_matches_oracle(op):
     """Runs shorter and longer than one warp's share, ragged tails inside a 128-byte row."""
     es = 8 if op == "affine_u32" else 4
     for w in warp_ws(op):
-        for n in (w, w + 40, 2048 + 7, 3 * 8192 + 17, 100_003):
+        for n in (w, w + 40, 2048 + 7, 3 * 8192 + 17, 100_003, 7 * w):
             x, ref = oracle_sliding(op, w, n, 13, op in INT_OPS)
             if n * es < 128:  # less than one 128-byte row: not for the tensor copies
                 with pytest.raises(B.SwsError, match="UNSUPPORTED"):
@@ -177,6 +178,6 @@ def test_warp_variant_many_tiles_per_warp(op):
 
 def test_warp_variant_unsupported_shapes():
     x = make_input("add_i32", 1 << 20, device="cuda")
-    for w, xv in ((48, x), (1024, x), (64, x[1:]), (16, x[:20])):
+    for w, xv in ((48, x), (96, x), (8192, x), (64, x[1:]), (16, x[:20])):
         with pytest.raises(B.SwsError, match="UNSUPPORTED"):
             B.sliding_sum("add_i32", w, xv, variant="warp")
