@@ -76,6 +76,8 @@ def load(path: str | None = None):
         lib.oracle_minimizers_from_keys.argtypes = [vp, u64, i32, vp, vp, u64]
         lib.oracle_kmer_table.restype = i32
         lib.oracle_kmer_table.argtypes = [vp, vp, u64, i32, i32, vp, vp, vp]
+        lib.oracle_seed_hits.restype = u64
+        lib.oracle_seed_hits.argtypes = [vp, vp, u64, vp, u64, ctypes.c_uint32, vp, vp, vp, u64]
         if path is None:
             _lib = lib
         return lib
@@ -221,3 +223,22 @@ def kmer_table(hashes, pos, hash_bits: int, bucket_bits: int, lib=None):
     if rc != 0:
         raise ValueError("bad bucket_bits")
     return sh[:m], sp[:m], off
+
+
+def seed_hits(ref_hash, ref_pos, query_hash, max_occ: int = 0, lib=None):
+    """Seed hits (query index, reference position) of each query seed against the reference's
+    (hash, position) seeds, seeds with more than max_occ hits skipped (0: no limit).
+    Returns (count per query before the filter, hit_query, hit_pos)."""
+    lib = lib or load()
+    h = np.ascontiguousarray(_np(ref_hash).astype(np.uint64))
+    p = np.ascontiguousarray(_np(ref_pos).astype(np.uint32))
+    q = np.ascontiguousarray(_np(query_hash).astype(np.uint64))
+    m, nq = h.size, q.size
+    cnt = np.zeros(max(nq, 1), dtype=np.uint32)
+    # first pass sizes the output
+    total = int(lib.oracle_seed_hits(_ptr(h), _ptr(p), m, _ptr(q), nq, int(max_occ), _ptr(cnt), None, None, 0))
+    hq = np.zeros(max(total, 1), dtype=np.uint32)
+    hp = np.zeros(max(total, 1), dtype=np.uint32)
+    got = int(lib.oracle_seed_hits(_ptr(h), _ptr(p), m, _ptr(q), nq, int(max_occ), _ptr(cnt), _ptr(hq), _ptr(hp), total))
+    assert got == total
+    return cnt[:nq], hq[:total], hp[:total]

@@ -429,3 +429,45 @@ int oracle_kmer_table(const uint64_t *hash, const uint32_t *pos, uint64_t m, int
     free(t);
     return 0;
 }
+
+/* Seed hits of the seeding stage (Sec. 2.3), through the seed table of Sec. 2.4 (Fig. 1): the
+ * hits of query seed i (hash qh[i]) are the reference positions j whose seed hash equals qh[i].
+ * A seed with more than max_occ hits is skipped (max_occ = 0: no limit), the usual filter for
+ * repeats.  count[i] receives the number of hits of query i before the filter.  The kept hits are
+ * written as (i, position) pairs in increasing i and, per query, increasing position; at most
+ * cap are written.  Returns the number of kept hits.  Steps: sort the reference's (hash, pos)
+ * pairs (the position table), then a binary search for each query's equal run. */
+uint64_t oracle_seed_hits(const uint64_t *ref_hash, const uint32_t *ref_pos, uint64_t m, const uint64_t *qh,
+                          uint64_t nq, uint32_t max_occ, uint32_t *count, uint32_t *hit_query, uint32_t *hit_pos,
+                          uint64_t cap)
+{
+    pair_t *t;
+    uint64_t i, j, lo, hi, mid, a, out = 0;
+    t = (pair_t *)malloc((size_t)(m ? m : 1) * sizeof(pair_t));
+    for (i = 0; i < m; ++i) {
+        t[i].h = ref_hash[i];
+        t[i].p = ref_pos[i];
+    }
+    qsort(t, (size_t)m, sizeof(pair_t), pair_cmp);
+    for (i = 0; i < nq; ++i) {
+        lo = 0; /* first index with hash >= qh[i] */
+        hi = m;
+        while (lo < hi) {
+            mid = lo + (hi - lo) / 2;
+            if (t[mid].h < qh[i]) lo = mid + 1;
+            else hi = mid;
+        }
+        a = lo;
+        while (a < m && t[a].h == qh[i]) ++a;
+        count[i] = (uint32_t)(a - lo);
+        if (max_occ != 0 && a - lo > max_occ) continue;
+        for (j = lo; j < a; ++j, ++out) {
+            if (out < cap) {
+                hit_query[out] = (uint32_t)i;
+                hit_pos[out] = t[j].p;
+            }
+        }
+    }
+    free(t);
+    return out;
+}

@@ -517,6 +517,32 @@ def check_table(lib):
             assert (int(h[i]), int(p[i])) in set(zip(sh[lo:hi].tolist(), sp[lo:hi].tolist()))
 
 
+def check_seed_hits(lib):
+    """Seed hits against a brute force over a dict: query i hits every reference position whose
+    seed hash equals its own, seeds with more than max_occ hits skipped; pairs in query order,
+    positions ascending."""
+    rng = np.random.default_rng(17)
+    for m, nq, hi, max_occ in ((0, 5, 4, 0), (1, 1, 1, 0), (400, 120, 30, 0), (400, 120, 30, 15), (3000, 500, 1 << 38, 0),
+                               (2000, 300, 8, 250)):
+        h = rng.integers(0, hi, size=m, dtype=np.uint64)
+        p = rng.permutation(1 << 20)[:m].astype(np.uint32)
+        q = rng.integers(0, hi + 2, size=nq, dtype=np.uint64)
+        if m:
+            q[::3] = h[rng.integers(0, m, size=q[::3].size)]
+        table = {}
+        for hv, pv in zip(h.tolist(), p.tolist()):
+            table.setdefault(hv, []).append(pv)
+        exp_cnt, exp_pairs = [], []
+        for i, qv in enumerate(q.tolist()):
+            hits = sorted(table.get(qv, []))
+            exp_cnt.append(len(hits))
+            if max_occ == 0 or len(hits) <= max_occ:
+                exp_pairs += [(i, x) for x in hits]
+        cnt, hq, hp = O.seed_hits(h, p, q, max_occ, lib=lib)
+        assert cnt.tolist() == exp_cnt
+        assert list(zip(hq.tolist(), hp.tolist())) == exp_pairs
+
+
 ALL_CHECKS = [
     check_eq2_vs_algorithms,
     check_eq2_closed_forms,
@@ -530,4 +556,5 @@ ALL_CHECKS = [
     check_fig2_example,
     check_batch_and_keys,
     check_table,
+    check_seed_hits,
 ]

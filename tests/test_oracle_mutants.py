@@ -81,6 +81,14 @@ MUTANTS = [
      "offsets[(t[i].h >> shift) + 1]++;",
      "offsets[(t[i].h >> shift)]++;",
      [pins.check_table]),
+    ("seed_filter_inclusive",
+     "if (max_occ != 0 && a - lo > max_occ) continue;",
+     "if (max_occ != 0 && a - lo >= max_occ) continue;",
+     [pins.check_seed_hits]),
+    ("seed_search_upper_bound",
+     "if (t[mid].h < qh[i]) lo = mid + 1;",
+     "if (t[mid].h <= qh[i]) lo = mid + 1;",
+     [pins.check_seed_hits]),
     ("batch_positions_global",
      "run_minimizers_naive(s, (uint64_t)offs[r], (uint64_t)offs[r + 1], k, w, mode, (uint64_t)offs[r], &o);",
      "run_minimizers_naive(s, (uint64_t)offs[r], (uint64_t)offs[r + 1], k, w, mode, 0, &o);",
