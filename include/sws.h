@@ -275,6 +275,32 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
                           int bucket_bits, void *sorted_hash, uint32_t *sorted_pos, uint64_t *bucket_offsets,
                           void *stream);
 
+/* ---- seeding (Sec. 2.3) with the seed table (Sec. 2.4, Fig. 1) ------------------------------ */
+
+/* Seed lookup: for each of nq query seeds, the run of its hits in a position table built by
+ * sws_kmer_table (same hash_bits and bucket_bits): the pointer table gives the bucket's range and
+ * two binary searches the run of equal hashes.
+ *   sorted_hash, bucket_offsets : the table (device; sorted_hash uint32 when hash_bits <= 32,
+ *                                 else uint64; m entries; offsets 2^bucket_bits + 1).
+ *   query_hash : device, nq seeds of the same type.  A hash outside [0, 2^hash_bits) has no hits.
+ *   first, count : device outputs, nq each: query i's hits are sorted_pos[first[i] ..
+ *                  first[i] + count[i]) of the table (positions ascending within the run).
+ * Limits as sws_kmer_table.  Uses no workspace. */
+sws_status sws_seed_lookup(sws_ctx *ctx, const void *sorted_hash, uint64_t m, int hash_bits, int bucket_bits,
+                           const uint64_t *bucket_offsets, const void *query_hash, uint64_t nq, uint64_t *first,
+                           uint32_t *count, void *stream);
+
+/* Seed hits: expand the runs found by sws_seed_lookup into (query index, reference position)
+ * pairs, in query order and, per query, position order.  A seed with more than max_occ hits is
+ * skipped (the usual repeat filter; max_occ = 0: no limit).
+ *   first, count : device, from sws_seed_lookup;  sorted_pos : device, the table's positions.
+ *   hit_query, hit_pos : device outputs; at most `capacity` pairs are written.
+ *   hit_count : device uint64 receiving the exact number of kept pairs (also when > capacity).
+ * nq < 2^32.  Uses workspace (8 bytes per 1024 queries). */
+sws_status sws_seed_hits(sws_ctx *ctx, const uint64_t *first, const uint32_t *count, uint64_t nq, uint32_t max_occ,
+                         const uint32_t *sorted_pos, uint32_t *hit_query, uint32_t *hit_pos, uint64_t capacity,
+                         uint64_t *hit_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,8 @@ SIGNATURES = {
     "sws_sync": (i32, [vp, vp]),
     "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
     "sws_selftest_wait_timeout": (i32, [vp, i32, vp]),
+    "sws_seed_lookup": (i32, [vp, vp, u64, i32, i32, vp, vp, u64, vp, vp, vp]),
+    "sws_seed_hits": (i32, [vp, vp, vp, u64, ctypes.c_uint32, vp, vp, vp, u64, vp, vp]),
     "sws_kmers": (i32, [vp, vp, u64, i32, i32, vp, vp]),
     "sws_minimizers": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
     "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
@@ -437,3 +439,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def seed_lookup(sorted_hash: torch.Tensor, offsets: torch.Tensor, hash_bits: int, bucket_bits: int,
+                query_hash: torch.Tensor, ctx: Context | None = None, stream=None):
+    """(first int64, count int32) of each query seed's run in a table from :func:`kmer_table`."""
+    _dev(sorted_hash, "sorted_hash")
+    _dev(query_hash, "query_hash")
+    ctx = ctx or default_context(query_hash.device.index)
+    nq = query_hash.shape[0]
+    first = torch.empty(max(nq, 1), dtype=torch.int64, device=query_hash.device)
+    count = torch.empty(max(nq, 1), dtype=torch.int32, device=query_hash.device)
+    _check(load().sws_seed_lookup(ctx.handle, _ptr(sorted_hash), sorted_hash.shape[0], int(hash_bits), int(bucket_bits),
+                                  _ptr(offsets), _ptr(query_hash), nq, _ptr(first), _ptr(count), _stream(stream)))
+    return first[:nq], count[:nq]
+
+
+def seed_hits(first: torch.Tensor, count: torch.Tensor, sorted_pos: torch.Tensor, max_occ: int = 0,
+              capacity: int | None = None, ctx: Context | None = None, stream=None, sync: bool = True):
+    """(hit_query, hit_pos) pairs of the runs from :func:`seed_lookup` (seeds with more than
+    max_occ hits skipped).  With ``sync=False`` returns the untrimmed buffers and the count."""
+    _dev(first, "first")
+    ctx = ctx or default_context(first.device.index)
+    nq = first.shape[0]
+    if capacity is None:
+        capacity = int(count.to(torch.int64).sum().item()) if nq else 0
+    hq = torch.empty(max(capacity, 1), dtype=torch.int32, device=first.device)
+    hp = torch.empty(max(capacity, 1), dtype=torch.int32, device=first.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=first.device)
+    if sorted_pos.numel() == 0:  # an empty table: every count is 0, the array is never read
+        sorted_pos = torch.zeros(1, dtype=torch.int32, device=first.device)
+    _check(load().sws_seed_hits(ctx.handle, _ptr(first), _ptr(count), nq, int(max_occ) & 0xFFFFFFFF, _ptr(sorted_pos),
+                                _ptr(hq), _ptr(hp), capacity, _ptr(cnt), _stream(stream)))
+    if not sync:
+        return hq, hp, cnt
+    ctx.sync(stream)
+    c = int(cnt.item())
+    if c > capacity:
+        raise SwsError(SWS_ERR_CAPACITY, f"{c} hits exceed the capacity {capacity}")
+    return hq[:c], hp[:c]

@@ -435,4 +435,41 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
   return SWS_OK;
 }
 
+sws_status sws_seed_lookup(sws_ctx *ctx, const void *sorted_hash, uint64_t m, int hash_bits, int bucket_bits,
+                           const uint64_t *bucket_offsets, const void *query_hash, uint64_t nq, uint64_t *first,
+                           uint32_t *count, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (hash_bits < 1 || hash_bits > 64) return fail(SWS_ERR_INVALID, "hash_bits must be in [1, 64] (got %d)", hash_bits);
+  if (bucket_bits < 0 || bucket_bits > hash_bits || bucket_bits > 32)
+    return fail(SWS_ERR_INVALID, "bucket_bits must be in [0, min(hash_bits, 32)] (got %d)", bucket_bits);
+  if (m >= (1ull << 32)) return fail(SWS_ERR_INVALID, "at most 2^32 - 1 table entries");
+  if (nq == 0) return SWS_OK;
+  if (!bucket_offsets || !query_hash || !first || !count || (m > 0 && !sorted_hash))
+    return fail(SWS_ERR_INVALID, "NULL array");
+  cudaError_t e = sws::launch_seed_lookup(sorted_hash, hash_bits, bucket_bits, bucket_offsets, query_hash, nq, first,
+                                          count, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "seed-lookup launch");
+  return SWS_OK;
+}
+
+sws_status sws_seed_hits(sws_ctx *ctx, const uint64_t *first, const uint32_t *count, uint64_t nq, uint32_t max_occ,
+                         const uint32_t *sorted_pos, uint32_t *hit_query, uint32_t *hit_pos, uint64_t capacity,
+                         uint64_t *hit_count, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (nq >= (1ull << 32)) return fail(SWS_ERR_INVALID, "at most 2^32 - 1 queries");
+  if (!hit_count) return fail(SWS_ERR_INVALID, "hit_count is NULL");
+  if (nq > 0 && (!first || !count || !sorted_pos)) return fail(SWS_ERR_INVALID, "NULL array");
+  if (capacity > 0 && (!hit_query || !hit_pos)) return fail(SWS_ERR_INVALID, "hit_query/hit_pos is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t bytes = round_up(sws::seed_hit_tiles(nq) * 8, 256) + 256;
+  s = ensure_ws(ctx, bytes, st);
+  if (s) return s;
+  cudaError_t e = sws::launch_seed_hits(first, count, nq, max_occ, sorted_pos, hit_query, hit_pos, capacity, hit_count,
+                                        static_cast<unsigned long long *>(ctx->ws), st);
+  if (e != cudaSuccess) return cuda_fail(e, "seed-hits launch");
+  return SWS_OK;
+}
+
 }  // extern "C"

@@ -127,6 +127,14 @@ uint64_t table_bsum_words(uint64_t m);
 uint64_t table_gap_bytes(int bucket_bits);
 cudaError_t launch_table(const TableArgs &a, cudaStream_t stream);
 
+// Seeding (seed.cu).
+uint64_t seed_hit_tiles(uint64_t nq);  // 8 bytes of workspace each
+cudaError_t launch_seed_lookup(const void *sorted_hash, int hash_bits, int bucket_bits, const uint64_t *offsets,
+                               const void *query, uint64_t nq, uint64_t *first, uint32_t *count, cudaStream_t stream);
+cudaError_t launch_seed_hits(const uint64_t *first, const uint32_t *count, uint64_t nq, uint32_t max_occ,
+                             const uint32_t *sorted_pos, uint32_t *hit_query, uint32_t *hit_pos, uint64_t capacity,
+                             uint64_t *hit_count, unsigned long long *tile_ws, cudaStream_t stream);
+
 // Error reporting and argument checks shared with api.cu (sws_status is an int).
 int report_error(int status, const char *msg);
 int check_minimizer_args(int k, int w, int mode);
