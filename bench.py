@@ -478,11 +478,45 @@ def genome_table_extras(dev, ctx, n: int = 3_100_000_000, reps: int = 3, bucket_
                              "table_mhits_s": round(m / (ms_t / 1e3) / 1e6, 1),
                              "gbp_s": round(n / ((ms_m + ms_t) / 1e3) / 1e9, 1),
                              "hit_bytes": hb + 4}
+        if k == 19:
+            out["seeding_k19_w10"] = seeding_extras(seq, n, k, w, h, p, bucket_bits, ctx, stream, reps)
         del h, p, cnt
         torch.cuda.empty_cache()
     del seq, nb
     torch.cuda.empty_cache()
     return out
+
+
+def seeding_extras(seq, n, k, w, gh, gp, bucket_bits, ctx, stream, reps, n_reads: int = 1_000_000):
+    """Seeding (Sec. 2.3) against the genome's seed table: 1e6 reads of 100-248 bases (multiples
+    of 4) cut from the genome at byte boundaries, their minimizers in one batch, each minimizer
+    looked up in the table, hits expanded with a repeat filter of 1000."""
+    import paper_1811_10074_gb300 as P
+    dev = seq.device
+    sh, sp, off = P.kmer_table(gh, gp, 2 * k, bucket_bits, ctx=ctx, stream=stream)
+    g = torch.Generator(device=dev)
+    g.manual_seed(42)
+    lens_b = torch.randint(25, 63, (n_reads,), generator=g, device=dev)          # bytes (4 bases each)
+    starts_b = torch.randint(0, n // 4 - 64, (n_reads,), generator=g, device=dev)
+    ends = torch.cumsum(lens_b, 0)
+    idx = torch.repeat_interleave(starts_b - (ends - lens_b), lens_b) + torch.arange(int(ends[-1]), device=dev)
+    rseq = seq[idx]
+    offs = torch.cat([torch.zeros(1, dtype=torch.int64, device=dev), ends * 4])
+    total = int(offs[-1])
+    qh, qp, po = P.minimizers_batch(rseq, offs, total, k, w, ctx=ctx, stream=stream)
+    nq = qh.shape[0]
+    look = lambda: P.seed_lookup(sh, off, 2 * k, bucket_bits, qh, ctx=ctx, stream=stream)
+    ms_l = time_call(look, reps, stream)
+    first, count = look()
+    cap = int(count.to(torch.int64).sum().item())
+    hitsf = lambda: P.seed_hits(first, count, sp, 1000, capacity=cap, ctx=ctx, stream=stream, sync=False)
+    ms_h = time_call(hitsf, reps, stream)
+    _, _, hc = hitsf()
+    nh = int(hc.item())
+    return {"reads": n_reads, "read_bases": total, "query_seeds": nq, "seeds_with_hits": int((count > 0).sum().item()),
+            "lookup_ms": round(ms_l, 3), "lookups_per_s": round(nq / (ms_l / 1e3) / 1e6, 1),
+            "hits": nh, "hits_ms": round(ms_h, 3), "hits_per_s_m": round(nh / (ms_h / 1e3) / 1e6, 1),
+            "unit": "lookups_per_s and hits_per_s_m in millions per second"}
 
 
 def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain_sample: int = 20_000, reps: int = 5):
