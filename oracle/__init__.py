@@ -76,6 +76,8 @@ def load(path: str | None = None):
         lib.oracle_minimizers_from_keys.argtypes = [vp, u64, i32, vp, vp, u64]
         lib.oracle_kmer_table.restype = i32
         lib.oracle_kmer_table.argtypes = [vp, vp, u64, i32, i32, vp, vp, vp]
+        lib.oracle_strands.restype = None
+        lib.oracle_strands.argtypes = [vp, u64, i32, vp, vp, u64, vp, u64, vp]
         lib.oracle_seed_hits.restype = u64
         lib.oracle_seed_hits.argtypes = [vp, vp, u64, vp, u64, ctypes.c_uint32, vp, vp, vp, u64]
         if path is None:
@@ -242,3 +244,19 @@ def seed_hits(ref_hash, ref_pos, query_hash, max_occ: int = 0, lib=None):
     got = int(lib.oracle_seed_hits(_ptr(h), _ptr(p), m, _ptr(q), nq, int(max_occ), _ptr(cnt), _ptr(hq), _ptr(hp), total))
     assert got == total
     return cnt[:nq], hq[:total], hp[:total]
+
+
+def strands(seq, n: int, k: int, pos, offs=None, pick_offs=None, lib=None) -> np.ndarray:
+    """Strand (0 forward / palindrome, 1 reverse complement, 255 outside) of each pick."""
+    lib = lib or load()
+    s = _np(seq, np.uint8)
+    pv = np.ascontiguousarray(_np(pos).astype(np.uint32))
+    m = pv.size
+    out = np.zeros(max(m, 1), dtype=np.uint8)
+    if offs is None:
+        lib.oracle_strands(_ptr(s), n, k, None, None, 0, _ptr(pv), m, _ptr(out))
+    else:
+        o = np.ascontiguousarray(np.asarray(offs, dtype=np.int64))
+        po = np.ascontiguousarray(np.asarray(pick_offs, dtype=np.uint64))
+        lib.oracle_strands(_ptr(s), n, k, _ptr(o), _ptr(po), o.size - 1, _ptr(pv), m, _ptr(out))
+    return out[:m]

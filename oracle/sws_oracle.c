@@ -471,3 +471,35 @@ uint64_t oracle_seed_hits(const uint64_t *ref_hash, const uint32_t *ref_pos, uin
     free(t);
     return out;
 }
+
+/* Strand of a minimizer pick (Sec. 2.4; minimizers over canonical k-mers pick min(forward,
+ * reverse complement)): 0 when the forward k-mer at the pick is the smaller or they are equal (a
+ * palindrome), 1 when its reverse complement is the smaller.  Picks of one sequence (offs = NULL:
+ * base = pos[i]) or of a read batch (read r holds picks pick_offs[r] .. pick_offs[r+1]-1 and
+ * starts at base offs[r]; pos is read-local).  A pick whose k-mer does not lie inside the
+ * sequence gets 255. */
+void oracle_strands(const uint8_t *s, uint64_t n, int k, const int64_t *offs, const uint64_t *pick_offs, uint64_t nreads,
+                    const uint32_t *pos, uint64_t m, uint8_t *strand)
+{
+    uint64_t i, r = 0, base, f, rc;
+    int j, b;
+    for (i = 0; i < m; ++i) {
+        base = pos[i];
+        if (offs) {
+            while (r + 1 < nreads && pick_offs[r + 1] <= i) ++r;
+            base += (uint64_t)offs[r];
+        }
+        if (base + (uint64_t)k > n) {
+            strand[i] = 255;
+            continue;
+        }
+        f = 0;
+        rc = 0;
+        for (j = 0; j < k; ++j) {
+            b = base_at(s, base + (uint64_t)j);
+            f = f * 4 + (uint64_t)b;                    /* first base most significant */
+            rc = rc + ((uint64_t)(3 - b) << (2 * j));  /* complement, read backwards */
+        }
+        strand[i] = rc < f ? 1 : 0;
+    }
+}

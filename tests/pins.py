@@ -543,6 +543,45 @@ def check_seed_hits(lib):
         assert list(zip(hq.tolist(), hp.tolist())) == exp_pairs
 
 
+def check_strands(lib):
+    """Strand of canonical picks against strings: 1 iff the reverse complement is smaller."""
+    rng = np.random.default_rng(23)
+    comp = {"A": "T", "C": "G", "G": "C", "T": "A"}
+    for k in (1, 2, 5, 6, 15, 19, 32):
+        n = 300
+        codes = rng.integers(0, 4, size=n)
+        st = "".join("ACGT"[c] for c in codes)
+        packed = pack_string(st)
+        pos = rng.integers(0, n - k + 1, size=60).astype(np.uint32)
+        pos = np.concatenate([pos, [n - k + 1, n]]).astype(np.uint32)  # two outside the sequence
+        got = O.strands(packed, n, k, pos, lib=lib)
+        for i, p in enumerate(pos.tolist()):
+            if p + k > n:
+                assert got[i] == 255
+                continue
+            f = st[p:p + k]
+            r = "".join(comp[c] for c in reversed(f))
+            assert got[i] == (1 if r < f else 0), (k, p, f, r)
+    # a batch: read-local positions
+    lens = [40, 0, 25, 60]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    codes = rng.integers(0, 4, size=int(offs[-1]))
+    packed = pack_string("".join("ACGT"[c] for c in codes))
+    k = 7
+    pos, po = [], [0]
+    for L in lens:
+        q = list(range(0, max(L - k + 1, 0), 3))
+        pos += q
+        po.append(po[-1] + len(q))
+    got = O.strands(packed, int(offs[-1]), k, np.array(pos, np.uint32), offs, np.array(po, np.uint64), lib=lib)
+    st = "".join("ACGT"[c] for c in codes)
+    for r in range(len(lens)):
+        for i in range(po[r], po[r + 1]):
+            f = st[offs[r] + pos[i]:offs[r] + pos[i] + k]
+            rc = "".join(comp[c] for c in reversed(f))
+            assert got[i] == (1 if rc < f else 0)
+
+
 ALL_CHECKS = [
     check_eq2_vs_algorithms,
     check_eq2_closed_forms,
@@ -557,4 +596,5 @@ ALL_CHECKS = [
     check_batch_and_keys,
     check_table,
     check_seed_hits,
+    check_strands,
 ]

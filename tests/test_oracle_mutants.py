@@ -89,6 +89,10 @@ MUTANTS = [
      "if (t[mid].h < qh[i]) lo = mid + 1;",
      "if (t[mid].h <= qh[i]) lo = mid + 1;",
      [pins.check_seed_hits]),
+    ("strand_forward_complement_order",
+     "rc = rc + ((uint64_t)(3 - b) << (2 * j));  /* complement, read backwards */",
+     "rc = rc * 4 + (uint64_t)(3 - b);",
+     [pins.check_strands]),
     ("batch_positions_global",
      "run_minimizers_naive(s, (uint64_t)offs[r], (uint64_t)offs[r + 1], k, w, mode, (uint64_t)offs[r], &o);",
      "run_minimizers_naive(s, (uint64_t)offs[r], (uint64_t)offs[r + 1], k, w, mode, 0, &o);",
