@@ -275,6 +275,20 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
                           int bucket_bits, void *sorted_hash, uint32_t *sorted_pos, uint64_t *bucket_offsets,
                           void *stream);
 
+/* Strand of each minimizer pick (Sec. 2.4 over canonical k-mers, which pick the smaller of the
+ * forward k-mer and its reverse complement): 0 when the forward k-mer at the pick is the smaller
+ * or they are equal (a palindrome, possible for even k), 1 when the reverse complement is.
+ *   seq, n, k  : the 2-bit packed sequence (or read batch) the picks came from, 1 <= k <= 32.
+ *   base_offsets, pick_offsets, nreads : NULL/NULL/0 for picks of one sequence (pos = base
+ *                index); for a batch, the read offsets (nreads + 1) and the pick offsets from
+ *                sws_minimizers_batch (pos read-local).
+ *   pos, m     : device, the picks' positions.  strand_out : device uint8 [m]; a pick whose k-mer
+ *                does not lie inside the sequence gets 255.
+ * Uses no workspace. */
+sws_status sws_minimizer_strands(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, const int64_t *base_offsets,
+                                 const uint64_t *pick_offsets, uint64_t nreads, const uint32_t *pos, uint64_t m,
+                                 uint8_t *strand_out, void *stream);
+
 /* ---- seeding (Sec. 2.3) with the seed table (Sec. 2.4, Fig. 1) ------------------------------ */
 
 /* Seed lookup: for each of nq query seeds, the run of its hits in a position table built by

@@ -48,6 +48,7 @@ SIGNATURES = {
     "sws_sync": (i32, [vp, vp]),
     "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
     "sws_selftest_wait_timeout": (i32, [vp, i32, vp]),
+    "sws_minimizer_strands": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, u64, vp, vp]),
     "sws_seed_lookup": (i32, [vp, vp, u64, i32, i32, vp, vp, u64, vp, vp, vp]),
     "sws_seed_hits": (i32, [vp, vp, vp, u64, ctypes.c_uint32, vp, vp, vp, u64, vp, vp]),
     "sws_kmers": (i32, [vp, vp, u64, i32, i32, vp, vp]),
@@ -478,3 +479,18 @@ def seed_hits(first: torch.Tensor, count: torch.Tensor, sorted_pos: torch.Tensor
     if c > capacity:
         raise SwsError(SWS_ERR_CAPACITY, f"{c} hits exceed the capacity {capacity}")
     return hq[:c], hp[:c]
+
+
+def minimizer_strands(seq: torch.Tensor, n: int, k: int, pos: torch.Tensor, base_offsets: torch.Tensor | None = None,
+                      pick_offsets: torch.Tensor | None = None, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """uint8 strand of each pick: 0 forward (or palindrome), 1 reverse complement, 255 outside."""
+    _dev(seq, "seq")
+    ctx = ctx or default_context(seq.device.index)
+    m = pos.shape[0]
+    out = torch.empty(max(m, 1), dtype=torch.uint8, device=seq.device)
+    nreads = base_offsets.shape[0] - 1 if base_offsets is not None else 0
+    _check(load().sws_minimizer_strands(ctx.handle, _ptr(seq), int(n), int(k),
+                                        _ptr(base_offsets) if base_offsets is not None else vp(0),
+                                        _ptr(pick_offsets) if pick_offsets is not None else vp(0), nreads, _ptr(pos), m,
+                                        _ptr(out), _stream(stream)))
+    return out[:m]

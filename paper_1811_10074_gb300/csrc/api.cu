@@ -435,6 +435,23 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
   return SWS_OK;
 }
 
+sws_status sws_minimizer_strands(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, const int64_t *base_offsets,
+                                 const uint64_t *pick_offsets, uint64_t nreads, const uint32_t *pos, uint64_t m,
+                                 uint8_t *strand_out, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (k < 1 || k > 32) return fail(SWS_ERR_INVALID, "k must be in [1, 32] (got %d)", k);
+  if (m == 0) return SWS_OK;
+  if (!seq || !pos || !strand_out) return fail(SWS_ERR_INVALID, "NULL array");
+  if ((base_offsets == nullptr) != (pick_offsets == nullptr))
+    return fail(SWS_ERR_INVALID, "base_offsets and pick_offsets go together");
+  if (base_offsets && nreads == 0) return fail(SWS_ERR_INVALID, "a batch needs nreads >= 1");
+  cudaError_t e = sws::launch_strands(seq, n, k, base_offsets, pick_offsets, base_offsets ? nreads : 0, pos, m,
+                                      strand_out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "strand launch");
+  return SWS_OK;
+}
+
 sws_status sws_seed_lookup(sws_ctx *ctx, const void *sorted_hash, uint64_t m, int hash_bits, int bucket_bits,
                            const uint64_t *bucket_offsets, const void *query_hash, uint64_t nq, uint64_t *first,
                            uint32_t *count, void *stream) {

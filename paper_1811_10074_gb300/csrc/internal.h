@@ -135,6 +135,11 @@ cudaError_t launch_seed_hits(const uint64_t *first, const uint32_t *count, uint6
                              const uint32_t *sorted_pos, uint32_t *hit_query, uint32_t *hit_pos, uint64_t capacity,
                              uint64_t *hit_count, unsigned long long *tile_ws, cudaStream_t stream);
 
+// Strands of minimizer picks (strand.cu).
+cudaError_t launch_strands(const uint8_t *seq, uint64_t n, int k, const int64_t *base_offsets,
+                           const uint64_t *pick_offsets, uint64_t nreads, const uint32_t *pos, uint64_t m,
+                           uint8_t *strand, cudaStream_t stream);
+
 // Error reporting and argument checks shared with api.cu (sws_status is an int).
 int report_error(int status, const char *msg);
 int check_minimizer_args(int k, int w, int mode);

@@ -226,3 +226,30 @@ def test_key_minimizers_full_size_sampled():
         sel = (rp >= lo) & (rp < hi)
         i0, i1 = torch.searchsorted(pos, torch.tensor([lo, hi], device=pos.device)).tolist()
         assert (pos[i0:i1].cpu().numpy() == rp[sel]).all() and (to_u64(h[i0:i1]) == rh[sel]).all(), a
+
+
+@pytest.mark.parametrize("k", [5, 6, 15, 19, 32])
+def test_minimizer_strands(k):
+    """Strand of canonical picks (0 forward / palindrome, 1 reverse complement) against the oracle,
+    for one sequence and for a read batch."""
+    n = 300_000
+    seq = synth.acgt_uniform_packed(n, seed=k)
+    h, p = B.minimizers(seq.cuda(), n, k, 10, "canonical")
+    got = B.minimizer_strands(seq.cuda(), n, k, p).cpu().numpy()
+    ref = oracle.strands(seq, n, k, p.cpu().numpy().view(np.uint32))
+    assert (got == ref).all() and set(np.unique(ref).tolist()) <= {0, 1}
+    if k % 2 == 1:
+        assert 0.4 < ref.mean() < 0.6  # both strands equally likely for random sequence
+    rng = np.random.default_rng(k)
+    lens = rng.integers(0, 300, size=500)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    bseq = synth.acgt_uniform_packed(int(offs[-1]), seed=k + 1)
+    od = torch.from_numpy(offs).cuda()
+    bh, bp, bpo = B.minimizers_batch(bseq.cuda(), od, int(offs[-1]), k, 10, "canonical")
+    got = B.minimizer_strands(bseq.cuda(), int(offs[-1]), k, bp, od, bpo).cpu().numpy()
+    ref = oracle.strands(bseq, int(offs[-1]), k, bp.cpu().numpy().view(np.uint32), offs,
+                         bpo.cpu().numpy().view(np.uint64))
+    assert (got == ref).all()
+    # positions outside the sequence
+    bad = torch.tensor([n - k + 1, n], dtype=torch.int32, device="cuda")
+    assert B.minimizer_strands(seq.cuda(), n, k, bad).tolist() == [255, 255]
