@@ -72,7 +72,8 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
 #define SWS_OP_ADD_F32 5
 
 /* Algorithm variants. */
-#define SWS_VARIANT_AUTO 0          /* the library's choice (block combine: in registers for w <= 8,
+#define SWS_VARIANT_AUTO 0          /* the variant sws_tune_sliding_sum chose for (op, w), else the
+                                       library's rule (block combine: in registers for w <= 8,
                                        warp-private or CTA streams on large inputs, one-shot tiles
                                        otherwise)                                                  */
 #define SWS_VARIANT_BLOCK_COMBINE 1 /* blocks of w: in-block suffix + next-block prefix, O(1)/output;
@@ -100,6 +101,20 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
  * returns; the next sws_sync on that stream returns SWS_ERR_TIMEOUT (and clears the word) and the
  * context stays usable.  Nothing faults, traps or hangs.  which outside {0, 1}: SWS_ERR_INVALID. */
 sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream);
+
+#define SWS_VARIANT_COUNT 6
+
+/* Autotuner for the sliding sum: runs every variant that applies to (op, w) on a scratch input
+ * of n elements (a fixed pseudo-random pattern in the context's workspace), times each (best of
+ * three launches on `stream`, CUDA events), and remembers the fastest for (op, w) in the context:
+ * later SWS_VARIANT_AUTO calls with this op and w and at least n/8 elements use it.  Blocks until
+ * the timing is done.
+ *   variant_out : optional, the chosen SWS_VARIANT_*.
+ *   ms_out      : optional, SWS_VARIANT_COUNT floats: milliseconds per variant, -1 where it does
+ *                 not apply (and for AUTO).
+ * Uses workspace (2 n elements).  w too large for this build: SWS_ERR_UNSUPPORTED. */
+sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *variant_out, float *ms_out,
+                                void *stream);
 
 /* Eq. 2: out[p] = in[p] (+) in[p+1] (+) ... (+) in[p+w-1] for p = 0 .. n-w (n-w+1 outputs,
  * exactly w addends each, Sec. 2.2).

@@ -7,4 +7,4 @@ load the library; the first call does, and raises if it has not been built.
 
 from .binding import (Batch, Context, Server, SwsError, default_context, kmer_table, kmers,  # noqa: F401
                       minimizer_strands, minimizers, minimizers_batch, minimizers_from_keys, seed_hits,
-                      seed_lookup, sliding_sum)
+                      seed_lookup, sliding_sum, tune_sliding_sum)

@@ -47,6 +47,7 @@ SIGNATURES = {
     "sws_reserve": (i32, [vp, u64]),
     "sws_sync": (i32, [vp, vp]),
     "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
+    "sws_tune_sliding_sum": (i32, [vp, i32, i32, u64, vp, vp, vp]),
     "sws_selftest_wait_timeout": (i32, [vp, i32, vp]),
     "sws_minimizer_strands": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, u64, vp, vp]),
     "sws_seed_lookup": (i32, [vp, vp, u64, i32, i32, vp, vp, u64, vp, vp, vp]),
@@ -196,6 +197,17 @@ def sliding_sum(op: str, w: int, x: torch.Tensor, out: torch.Tensor | None = Non
     _check(load().sws_sliding_sum(ctx.handle, OPS[op], int(w), _ptr(x), _ptr(out), n, VARIANTS[variant],
                                   _stream(stream)))
     return out
+
+
+def tune_sliding_sum(op: str, w: int, n: int, ctx: Context | None = None, stream=None):
+    """Time every variant that applies to (op, w) on n scratch elements; the context then uses the
+    fastest for ``variant="auto"``.  Returns (chosen variant name, {variant name: ms})."""
+    ctx = ctx or default_context(torch.cuda.current_device())
+    chosen = ctypes.c_int(-1)
+    ms = (ctypes.c_float * len(VARIANTS))()
+    _check(load().sws_tune_sliding_sum(ctx.handle, OPS[op], int(w), int(n), ctypes.byref(chosen), ms, _stream(stream)))
+    names = {v: k for k, v in VARIANTS.items()}
+    return names[chosen.value], {names[i]: round(ms[i], 4) for i in range(len(VARIANTS)) if ms[i] >= 0}
 
 
 def selftest_wait_timeout(which: str = "lookback", ctx: Context | None = None, stream=None) -> None:

@@ -199,6 +199,11 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   L.variant = variant;
   L.num_sms = ctx->num_sms;
   L.err = ctx->d_err;
+  if (variant == SWS_VARIANT_AUTO) {  // a variant sws_tune_sliding_sum chose for this (op, w)
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tuned.find({op, w});
+    if (it != ctx->tuned.end() && n >= it->second.second / 8) L.variant = it->second.first;
+  }
   // the smaller tile when it keeps the halo re-read under an eighth of the tile
   const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
   L.cfg = (w - 1) * 8 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
@@ -210,6 +215,74 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
     return fail(SWS_ERR_UNSUPPORTED, "the streamed block combine does not apply to w = %d, n = %llu at this alignment",
                 w, (unsigned long long)n);
   if (e != cudaSuccess) return cuda_fail(e, "sliding-sum launch");
+  return SWS_OK;
+}
+
+sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *variant_out, float *ms_out,
+                                void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (op < SWS_OP_ADD_I32 || op > SWS_OP_ADD_F32) return fail(SWS_ERR_INVALID, "unknown operator %d", op);
+  if (w < 1) return fail(SWS_ERR_INVALID, "w must be >= 1 (got %d)", w);
+  if (n < (uint64_t)w) return fail(SWS_ERR_INVALID, "n must be >= w");
+  const int es = op_esize(op);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t in_bytes = round_up(n * (uint64_t)es, 256);
+  s = ensure_ws(ctx, 2 * in_bytes, st);
+  if (s) return s;
+  char *in = static_cast<char *>(ctx->ws);
+  char *out = in + in_bytes;
+  cudaError_t e = sws::launch_fill_pattern(in, n * (uint64_t)es, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning input");
+  sws::SlideLaunch L;
+  L.op = op;
+  L.num_sms = ctx->num_sms;
+  L.err = ctx->d_err;
+  const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
+  L.cfg = (w - 1) * 8 <= small_len ? sws::CFG_SMALL : sws::CFG_LARGE;
+  if (sws::slide_tile_outputs(L.cfg, es, w) == 0)
+    return fail(SWS_ERR_UNSUPPORTED, "w = %d is larger than the tile of this build", w);
+  cudaEvent_t e0, e1;
+  SWS_CUDA(cudaEventCreate(&e0));
+  SWS_CUDA(cudaEventCreate(&e1));
+  float ms[SWS_VARIANT_COUNT];
+  int best = -1;
+  for (int v = 0; v < SWS_VARIANT_COUNT; ++v) {
+    ms[v] = -1.0f;
+    if (v == SWS_VARIANT_AUTO) continue;
+    if (v == SWS_VARIANT_PREFIX_DIFF && op != SWS_OP_ADD_I32 && op != SWS_OP_XOR_I32) continue;
+    L.variant = v;
+    e = sws::launch_sliding_sum(L, in, out, n, w, st);  // warm-up; also tells whether v applies
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // v does not apply to (op, w, n)
+      cudaGetLastError();
+      e = cudaSuccess;
+      continue;
+    }
+    if (e != cudaSuccess) break;
+    float t = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = sws::launch_sliding_sum(L, in, out, n, w, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float x = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+      if (e == cudaSuccess && x < t) t = x;
+    }
+    if (e != cudaSuccess) break;
+    ms[v] = t;
+    if (best < 0 || t < ms[best]) best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning run");
+  if (best < 0) return fail(SWS_ERR_UNSUPPORTED, "no variant applies to w = %d", w);
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tuned[{op, w}] = {best, n};
+  }
+  if (variant_out) *variant_out = best;
+  if (ms_out) memcpy(ms_out, ms, sizeof(ms));
   return SWS_OK;
 }
 

@@ -1,6 +1,10 @@
 // internal.h -- declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -11,6 +15,10 @@ struct sws_ctx {
   void *ws = nullptr;    // workspace
   uint64_t ws_size = 0;
   int num_sms = 0;
+  // sliding-sum variants chosen by sws_tune_sliding_sum, per (operator, w): variant and the n
+  // it was timed on
+  std::mutex tune_mu;
+  std::map<std::pair<int, int>, std::pair<int, uint64_t>> tuned;
 };
 
 namespace sws {
@@ -30,6 +38,9 @@ struct SlideLaunch {
 int slide_tile_len(int cfg, int esize);
 // Outputs per tile, or 0 when w does not fit the configuration.
 int slide_tile_outputs(int cfg, int esize, int w);
+
+// Fill `bytes` of device memory with a fixed pseudo-random pattern (timing inputs).
+cudaError_t launch_fill_pattern(void *dst, uint64_t bytes, cudaStream_t stream);
 
 // Queue one sliding sum; the caller has validated the arguments.
 cudaError_t launch_sliding_sum(const SlideLaunch &L, const void *in, void *out, uint64_t n, int w,

@@ -1174,6 +1174,25 @@ cudaError_t launch_cfg(const SlideLaunch &L, const void *in, void *out, uint64_t
 
 }  // namespace
 
+namespace {
+// A splitmix-style finaliser of the word index: any fixed pattern works for timing.
+__global__ void k_fill_pattern(uint32_t *__restrict__ dst, uint64_t words) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    dst[i] = (uint32_t)(z ^ (z >> 31)) & 0x00FFFFFFu;  // small values: no float specials
+  }
+}
+}  // namespace
+
+cudaError_t launch_fill_pattern(void *dst, uint64_t bytes, cudaStream_t st) {
+  const uint64_t words = bytes / 4;
+  if (words == 0) return cudaSuccess;
+  k_fill_pattern<<<1024, 256, 0, st>>>(static_cast<uint32_t *>(dst), words);
+  return cudaGetLastError();
+}
+
 int slide_tile_len(int cfg, int esize) {
   if (cfg == CFG_SMALL) return esize == 4 ? Shape<CfgSmall, 4>::L : Shape<CfgSmall, 8>::L;
   return esize == 4 ? Shape<CfgLarge, 4>::L : Shape<CfgLarge, 8>::L;

@@ -181,3 +181,24 @@ def test_warp_variant_unsupported_shapes():
     for w, xv in ((48, x), (96, x), (8192, x), (64, x[1:]), (16, x[:20])):
         with pytest.raises(B.SwsError, match="UNSUPPORTED"):
             B.sliding_sum("add_i32", w, xv, variant="warp")
+
+
+# ---------------------------------------------------------------------------------------------
+# the autotuner
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("op,w", [("add_i32", 64), ("min_i32", 1024), ("xor_i32", 5), ("affine_u32", 48),
+                                  ("add_f32", 256)])
+def test_tuner_picks_an_applicable_variant_and_auto_uses_it(op, w):
+    ctx = B.Context(0)
+    try:
+        n = 1 << 22
+        chosen, ms = B.tune_sliding_sum(op, w, n, ctx=ctx)
+        assert chosen in ms and ms[chosen] == min(ms.values()) and all(v > 0 for v in ms.values())
+        assert "block_combine" in ms and "doubling" in ms
+        assert ("prefix_diff" in ms) == (op in ("add_i32", "xor_i32"))
+        x = make_input(op, n, seed=3, device="cuda")
+        y = B.sliding_sum(op, w, x, ctx=ctx)  # auto -> the tuned variant
+        torch.cuda.synchronize()
+        assert_sampled(op, w, x, y, sample_indices(n - w + 1, np.random.default_rng(w)))
+    finally:
+        ctx.close()
