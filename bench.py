@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (AUTO uses its fixed rule)")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
     ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "table", "batch", "serve"],
@@ -233,6 +234,10 @@ def run_ours(args, world, rank, local):
             if events is not None:
                 events[i][1].record(stream)
 
+    tuned = {}
+    if not args.no_tune:  # the library's autotuner picks the variant AUTO uses for each (op, w)
+        for op, w in cases:
+            tuned[f"{op}/w{w}"] = P.tune_sliding_sum(op, w, n, ctx=ctx, stream=stream)[0]
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
@@ -298,7 +303,7 @@ def run_ours(args, world, rank, local):
                      "traffic": None if traffic is None else round(traffic),
                      "algorithmic_bytes_per_launch": round(step_bytes / len(cases)),
                      "traffic_source": TRAFFIC_PROFILE["summary"] + " (2^26 capture scaled by elements)",
-                     "per_case_gbs": per_case},
+                     "per_case_gbs": per_case, "variant_per_case": tuned or "fixed rule (no tuning)"},
         "e2e": e2e,
         "gpu_launches": len(cases) * args.steps,
         "clocks": clk,

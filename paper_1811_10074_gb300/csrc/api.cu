@@ -202,7 +202,10 @@ sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *ou
   if (variant == SWS_VARIANT_AUTO) {  // a variant sws_tune_sliding_sum chose for this (op, w)
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto it = ctx->tuned.find({op, w});
-    if (it != ctx->tuned.end() && n >= it->second.second / 8) L.variant = it->second.first;
+    if (it != ctx->tuned.end() && n >= it->second.n / 8) {
+      L.variant = it->second.variant;
+      L.shape = it->second.shape;
+    }
   }
   // the smaller tile when it keeps the halo re-read under an eighth of the tile
   const int small_len = sws::slide_tile_len(sws::CFG_SMALL, es);
@@ -246,32 +249,42 @@ sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *va
   SWS_CUDA(cudaEventCreate(&e0));
   SWS_CUDA(cudaEventCreate(&e1));
   float ms[SWS_VARIANT_COUNT];
-  int best = -1;
-  for (int v = 0; v < SWS_VARIANT_COUNT; ++v) {
+  int best = -1, best_shape = 0;
+  float best_t = 0.0f;
+  for (int v = 0; v < SWS_VARIANT_COUNT && e == cudaSuccess; ++v) {
     ms[v] = -1.0f;
     if (v == SWS_VARIANT_AUTO) continue;
     if (v == SWS_VARIANT_PREFIX_DIFF && op != SWS_OP_ADD_I32 && op != SWS_OP_XOR_I32) continue;
-    L.variant = v;
-    e = sws::launch_sliding_sum(L, in, out, n, w, st);  // warm-up; also tells whether v applies
-    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // v does not apply to (op, w, n)
-      cudaGetLastError();
-      e = cudaSuccess;
-      continue;
+    // the warp-private variant is timed in each of its run shapes; the others once
+    const int nshapes = v == SWS_VARIANT_BLOCK_COMBINE_WARP ? sws::kWarpShapes : 1;
+    for (int sh = 1; sh <= nshapes; ++sh) {
+      L.variant = v;
+      L.shape = v == SWS_VARIANT_BLOCK_COMBINE_WARP ? sh : 0;
+      e = sws::launch_sliding_sum(L, in, out, n, w, st);  // warm-up; also tells whether v applies
+      if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {  // v does not apply to (op, w, n)
+        cudaGetLastError();
+        e = cudaSuccess;
+        break;
+      }
+      if (e != cudaSuccess) break;
+      float t = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = sws::launch_sliding_sum(L, in, out, n, w, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float x = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (e == cudaSuccess && x < t) t = x;
+      }
+      if (e != cudaSuccess) break;
+      if (ms[v] < 0 || t < ms[v]) ms[v] = t;  // per variant: its best shape
+      if (best < 0 || t < best_t) {
+        best = v;
+        best_shape = L.shape;
+        best_t = t;
+      }
     }
-    if (e != cudaSuccess) break;
-    float t = 1e30f;
-    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-      e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) e = sws::launch_sliding_sum(L, in, out, n, w, st);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float x = 0;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
-      if (e == cudaSuccess && x < t) t = x;
-    }
-    if (e != cudaSuccess) break;
-    ms[v] = t;
-    if (best < 0 || t < ms[best]) best = v;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -279,7 +292,7 @@ sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *va
   if (best < 0) return fail(SWS_ERR_UNSUPPORTED, "no variant applies to w = %d", w);
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
-    ctx->tuned[{op, w}] = {best, n};
+    ctx->tuned[{op, w}] = {best, best_shape, n};
   }
   if (variant_out) *variant_out = best;
   if (ms_out) memcpy(ms_out, ms, sizeof(ms));

@@ -18,7 +18,11 @@ struct sws_ctx {
   // sliding-sum variants chosen by sws_tune_sliding_sum, per (operator, w): variant and the n
   // it was timed on
   std::mutex tune_mu;
-  std::map<std::pair<int, int>, std::pair<int, uint64_t>> tuned;
+  struct Tuned {
+    int variant, shape;
+    uint64_t n;
+  };
+  std::map<std::pair<int, int>, Tuned> tuned;
 };
 
 namespace sws {
@@ -32,7 +36,9 @@ struct SlideLaunch {
   int cfg;      // SlideCfg
   int num_sms;  // SMs of the device (grid of the persistent kernel)
   int *err;     // device error word (bounded waits)
+  int shape = 0;  // warp-private runs: 0 = chosen by block width, 1..3 = a fixed run shape
 };
+constexpr int kWarpShapes = 3;
 
 // Tile length (elements) of a configuration for elements of `esize` bytes.
 int slide_tile_len(int cfg, int esize);

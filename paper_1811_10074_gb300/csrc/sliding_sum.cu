@@ -1035,7 +1035,7 @@ cudaError_t launch_wblk_shape(const void *in, void *out, uint64_t n, int num_sms
 
 template <class Op>
 cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int num_sms, int *err, cudaStream_t st,
-                               bool quiet_unsupported) {
+                               bool quiet_unsupported, int shape) {
   using T = typename Op::T;
   constexpr int ES = (int)sizeof(T);
   constexpr int VPT = kStreamRowBytes / 2 / ES;  // 16 for 4-byte elements, 8 for affine pairs
@@ -1056,7 +1056,10 @@ cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int
   // prefixes even when n is a multiple of the warp-tile (that tile is then all identity)
   const uint64_t nwt = n / WT + 1;
   if (nwt * (uint64_t)(WT * ES / kStreamRowBytes) > 0x7fffffffull) return cudaErrorNotSupported;
-  const int sw = G == 1 ? 8 : (G <= 4 ? 4 : 2);  // warp-tiles per stage of the shape below
+  // run shapes (warps per CTA, warp-tiles per stage, stages): 1 = 4 x 8 x 2, 2 = 8 x 4 x 2,
+  // 3 = 16 x 2 x 3; by default narrow blocks take more bytes in flight per warp, wide ones more warps
+  if (shape < 1 || shape > kWarpShapes) shape = G == 1 ? 1 : (G <= 4 ? 2 : 3);
+  const int sw = shape == 1 ? 8 : (shape == 2 ? 4 : 2);  // warp-tiles per stage
   CUtensorMap map;
   const cuuint64_t gdim[2] = {kStreamRowBytes / 4, rows};
   const cuuint64_t gstride[1] = {kStreamRowBytes};
@@ -1067,8 +1070,8 @@ cudaError_t launch_warp_stream(const void *in, void *out, uint64_t n, int w, int
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const uint64_t n_full = rows * kStreamRowBytes / ES;
-  if (G == 1) return launch_warp_shape<Op, 4, 8, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
-  if (G <= 4) return launch_warp_shape<Op, 8, 4, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
+  if (shape == 1) return launch_warp_shape<Op, 4, 8, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
+  if (shape == 2) return launch_warp_shape<Op, 8, 4, 2>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
   return launch_warp_shape<Op, 16, 2, 3>(map, in, out, n, n_full, w, nwt, num_sms, err, st);
 }
 
@@ -1080,12 +1083,13 @@ cudaError_t launch_op(const SlideLaunch &SL, const void *in, void *out, uint64_t
   const int variant = SL.variant;
   if (variant == SWS_VARIANT_BLOCK_COMBINE_STREAM)
     return launch_stream<Op, S::NT, S::VPT, MINB>(in, out, n, w, SL.num_sms, SL.err, st, true);
-  if (variant == SWS_VARIANT_BLOCK_COMBINE_WARP) return launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true);
+  if (variant == SWS_VARIANT_BLOCK_COMBINE_WARP)
+    return launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true, SL.shape);
   if (variant == SWS_VARIANT_AUTO && !(w <= 8 && S::VPT % w == 0)) {
     // warp-private streaming when w's blocks fit a warp and the input fills the GPU a few times
     constexpr uint64_t WT = 32 * (kStreamRowBytes / 2 / sizeof(T));
     if (n / WT >= 64ull * (uint64_t)SL.num_sms) {
-      const cudaError_t e = launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true);
+      const cudaError_t e = launch_warp_stream<Op>(in, out, n, w, SL.num_sms, SL.err, st, true, SL.shape);
       if (e != cudaErrorNotSupported) return e;
     }
     // streamed when the grid fills the GPU at least twice; the one-shot tiles otherwise
