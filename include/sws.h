@@ -104,14 +104,16 @@ sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream);
 
 #define SWS_VARIANT_COUNT 6
 
-/* Autotuner for the sliding sum: runs every variant that applies to (op, w) on a scratch input
- * of n elements (a fixed pseudo-random pattern in the context's workspace), times each (best of
- * three launches on `stream`, CUDA events), and remembers the fastest for (op, w) in the context:
- * later SWS_VARIANT_AUTO calls with this op and w and at least n/8 elements use it.  Blocks until
- * the timing is done.
- *   variant_out : optional, the chosen SWS_VARIANT_*.
- *   ms_out      : optional, SWS_VARIANT_COUNT floats: milliseconds per variant, -1 where it does
- *                 not apply (and for AUTO).
+/* Autotuner for the sliding sum: on a scratch input of n elements (a fixed pseudo-random pattern
+ * in the context's workspace), after warming the GPU up with at least 10 ms of work, times the
+ * library's fixed rule and every variant that applies to (op, w) -- the warp-private variant in
+ * each of its run shapes -- (best of five launches on `stream`, CUDA events), and remembers for
+ * (op, w) the fastest if it beats the rule by more than 2% (else the rule): later
+ * SWS_VARIANT_AUTO calls with this op and w and at least n/8 elements use it.  Blocks until the
+ * timing is done.  Timings taken under a profiler that serialises launches are not meaningful.
+ *   variant_out : optional, the chosen SWS_VARIANT_* (SWS_VARIANT_AUTO: the rule stays).
+ *   ms_out      : optional, SWS_VARIANT_COUNT floats: milliseconds per variant (index 0: the
+ *                 rule), -1 where a variant does not apply.
  * Uses workspace (2 n elements).  w too large for this build: SWS_ERR_UNSUPPORTED. */
 sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *variant_out, float *ms_out,
                                 void *stream);

@@ -248,12 +248,42 @@ sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *va
   cudaEvent_t e0, e1;
   SWS_CUDA(cudaEventCreate(&e0));
   SWS_CUDA(cudaEventCreate(&e1));
+  // best of five launches of the current L, after one untimed launch; e carries errors
+  auto time_it = [&](float &t) {
+    t = 1e30f;
+    for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = sws::launch_sliding_sum(L, in, out, n, w, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float x = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+      if (e == cudaSuccess && x < t) t = x;
+    }
+  };
+  // the library's fixed rule (AUTO without a tuned entry) first, after warming the GPU up with
+  // at least 10 ms of it (clocks ramp from idle), so that every variant is timed at speed
   float ms[SWS_VARIANT_COUNT];
+  L.variant = SWS_VARIANT_AUTO;
+  L.shape = 0;
+  float warm = 0.0f;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int i = 0; i < 400 && e == cudaSuccess && warm < 10.0f; ++i) {
+    e = sws::launch_sliding_sum(L, in, out, n, w, st);
+    if (e == cudaSuccess && (i & 7) == 7) {
+      e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&warm, e0, e1);
+    }
+  }
+  float rule_t = 0.0f;
+  time_it(rule_t);
+  ms[SWS_VARIANT_AUTO] = rule_t;
   int best = -1, best_shape = 0;
   float best_t = 0.0f;
   for (int v = 0; v < SWS_VARIANT_COUNT && e == cudaSuccess; ++v) {
-    ms[v] = -1.0f;
     if (v == SWS_VARIANT_AUTO) continue;
+    ms[v] = -1.0f;
     if (v == SWS_VARIANT_PREFIX_DIFF && op != SWS_OP_ADD_I32 && op != SWS_OP_XOR_I32) continue;
     // the warp-private variant is timed in each of its run shapes; the others once
     const int nshapes = v == SWS_VARIANT_BLOCK_COMBINE_WARP ? sws::kWarpShapes : 1;
@@ -267,16 +297,8 @@ sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *va
         break;
       }
       if (e != cudaSuccess) break;
-      float t = 1e30f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-        e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) e = sws::launch_sliding_sum(L, in, out, n, w, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float x = 0;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
-        if (e == cudaSuccess && x < t) t = x;
-      }
+      float t = 0.0f;
+      time_it(t);
       if (e != cudaSuccess) break;
       if (ms[v] < 0 || t < ms[v]) ms[v] = t;  // per variant: its best shape
       if (best < 0 || t < best_t) {
@@ -290,6 +312,10 @@ sws_status sws_tune_sliding_sum(sws_ctx *ctx, int op, int w, uint64_t n, int *va
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(e, "tuning run");
   if (best < 0) return fail(SWS_ERR_UNSUPPORTED, "no variant applies to w = %d", w);
+  if (best_t > 0.98f * rule_t) {  // not clearly faster than the fixed rule: keep the rule
+    best = SWS_VARIANT_AUTO;
+    best_shape = 0;
+  }
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     ctx->tuned[{op, w}] = {best, best_shape, n};

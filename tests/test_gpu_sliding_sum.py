@@ -193,7 +193,9 @@ def test_tuner_picks_an_applicable_variant_and_auto_uses_it(op, w):
     try:
         n = 1 << 22
         chosen, ms = B.tune_sliding_sum(op, w, n, ctx=ctx)
-        assert chosen in ms and ms[chosen] == min(ms.values()) and all(v > 0 for v in ms.values())
+        assert chosen in ms and all(v > 0 for v in ms.values())
+        if chosen != "auto":  # a tuned variant must beat the fixed rule ("auto") by 2%
+            assert ms[chosen] == min(ms.values()) and ms[chosen] <= 0.98 * ms["auto"]
         assert "block_combine" in ms and "doubling" in ms
         assert ("prefix_diff" in ms) == (op in ("add_i32", "xor_i32"))
         x = make_input(op, n, seed=3, device="cuda")
