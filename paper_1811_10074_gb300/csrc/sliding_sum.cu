@@ -800,9 +800,8 @@ __global__ void __launch_bounds__(NT) k_slide_pd(const uint32_t *__restrict__ in
                                                  uint64_t n, int w, int TO) {
   constexpr int NW = NT / 32;
   constexpr int L = NT * VPT;
-  constexpr int PADL = L + NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw);  // running sums, padded
+  uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw);  // running sums, padded (L + NT words)
   __shared__ uint32_t wtot[NW];
   auto pad = [](int i) { return i + i / VPT; };
 
