@@ -244,6 +244,12 @@ sws_status sws_server_create(sws_ctx *ctx, const sws_server_config *cfg, sws_ser
 /* Queue a request (the bases are copied; the caller's buffer may be reused at once).
  * SWS_ERR_CAPACITY if nbases > max_bases_per_batch. */
 sws_status sws_server_submit(sws_server *s, const uint8_t *packed, uint64_t nbases, uint64_t *request_id);
+/* Queue `count` requests in one call: packed[i] holds nbases[i] bases (copied); their ids go to
+ * request_ids[i].  One lock and one wake-up for the lot; if any argument is wrong (a NULL
+ * sequence, a request longer than max_bases_per_batch: SWS_ERR_INVALID / SWS_ERR_CAPACITY)
+ * nothing is queued. */
+sws_status sws_server_submit_batch(sws_server *s, const uint8_t *const *packed, const uint64_t *nbases, uint64_t count,
+                                   uint64_t *request_ids);
 /* Wait up to timeout_s seconds (0: just look) for a request; *done = 1 once it is answered. */
 sws_status sws_server_wait(sws_server *s, uint64_t request_id, double timeout_s, int *done);
 /* Copy an answered request's picks to host buffers and forget the request. */

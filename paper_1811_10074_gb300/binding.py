@@ -65,6 +65,7 @@ SIGNATURES = {
     "sws_batch_sync": (i32, [vp]),
     "sws_server_create": (i32, [vp, vp, ctypes.POINTER(vp)]),
     "sws_server_submit": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
+    "sws_server_submit_batch": (i32, [vp, vp, vp, u64, vp]),
     "sws_server_wait": (i32, [vp, u64, ctypes.c_double, ctypes.POINTER(i32)]),
     "sws_server_result": (i32, [vp, u64, vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]),
     "sws_server_stats": (i32, [vp, vp]),
@@ -410,6 +411,17 @@ class Server:
         rid = u64()
         _check(load().sws_server_submit(self.handle, vp(arr.ctypes.data), int(nbases), ctypes.byref(rid)))
         return int(rid.value)
+
+    def submit_many(self, requests) -> list:
+        """Queue many (packed, nbases) requests in one call; returns their ids in order."""
+        import numpy as np
+        arrs = [np.ascontiguousarray(p.numpy() if hasattr(p, "numpy") else p, dtype=np.uint8) for p, _ in requests]
+        count = len(arrs)
+        ptrs = (vp * max(count, 1))(*[a.ctypes.data for a in arrs])
+        ns = (u64 * max(count, 1))(*[int(nb) for _, nb in requests])
+        ids = (u64 * max(count, 1))()
+        _check(load().sws_server_submit_batch(self.handle, ptrs, ns, count, ids))
+        return [int(ids[i]) for i in range(count)]
 
     def wait(self, rid: int, timeout: float = 60.0) -> bool:
         done = i32()

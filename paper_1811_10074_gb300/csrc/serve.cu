@@ -288,6 +288,42 @@ sws_status sws_server_submit(sws_server *s, const uint8_t *packed, uint64_t nbas
   return SWS_OK;
 }
 
+sws_status sws_server_submit_batch(sws_server *s, const uint8_t *const *packed, const uint64_t *nbases, uint64_t count,
+                                   uint64_t *request_ids) {
+  if (!s || (count && (!packed || !nbases || !request_ids))) return sws::report_error(SWS_ERR_INVALID, "NULL argument");
+  for (uint64_t i = 0; i < count; ++i) {
+    if (nbases[i] && !packed[i]) return sws::report_error(SWS_ERR_INVALID, "NULL sequence");
+    if (nbases[i] > s->cfg.max_bases_per_batch)
+      return sws::report_error(SWS_ERR_CAPACITY, "request longer than max_bases_per_batch");
+  }
+  std::vector<Request *> rs(count);
+  for (uint64_t i = 0; i < count; ++i) {  // copies outside the lock
+    Request *r = new Request();
+    r->seq.assign(packed[i], packed[i] + (nbases[i] + 3) / 4);
+    if (nbases[i] % 4) r->seq.back() &= (uint8_t)((1u << (2 * (nbases[i] % 4))) - 1u);
+    r->nbases = nbases[i];
+    rs[i] = r;
+  }
+  const Clock::time_point now = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->any && count) {
+      s->t_first = now;
+      s->any = true;
+    }
+    for (uint64_t i = 0; i < count; ++i) {
+      Request *r = rs[i];
+      r->t_submit = now;
+      r->id = s->next_id++;
+      s->reqs[r->id] = r;
+      s->pending.push_back(r);
+      request_ids[i] = r->id;
+    }
+  }
+  s->cv_work.notify_one();
+  return SWS_OK;
+}
+
 sws_status sws_server_wait(sws_server *s, uint64_t request_id, double timeout_s, int *done) {
   if (!s || !done) return sws::report_error(SWS_ERR_INVALID, "NULL argument");
   std::unique_lock<std::mutex> lock(s->mu);

@@ -73,3 +73,22 @@ def test_server_limits():
     srv.close()
     with pytest.raises(B.SwsError, match="UNSUPPORTED"):
         B.Server(19, 10)
+
+
+def test_submit_many_matches_single_submits():
+    rng = np.random.default_rng(21)
+    lens = rng.integers(0, 5000, size=200)
+    seqs = [synth.acgt_uniform_packed(int(L), seed=500 + i).numpy() for i, L in enumerate(lens)]
+    srv = B.Server(15, 10, slots=3, max_requests_per_batch=16, max_bases_per_batch=1 << 16)
+    try:
+        ids = srv.submit_many([(s, int(L)) for s, L in zip(seqs, lens)])
+        assert len(ids) == len(lens) and len(set(ids)) == len(ids)
+        for rid, s, L in zip(ids, seqs, lens):
+            assert srv.wait(rid, 60.0)
+            h, p, _ = srv.result(rid)
+            rh, rp = oracle.minimizers(s, int(L), 15, 10)
+            assert np.array_equal(h.astype(np.uint64), rh) and np.array_equal(p, rp)
+        with pytest.raises(B.SwsError, match="CAPACITY"):
+            srv.submit_many([(seqs[0], int(lens[0])), (np.zeros(1 << 15, np.uint8), 1 << 17)])
+    finally:
+        srv.close()
