@@ -70,6 +70,8 @@ struct sws_server {
   uint64_t inflight_bytes = 0;
   bool stop = false;
   std::thread worker;
+  // result buffers of retrieved requests, reused (already faulted in) for later results
+  std::vector<std::vector<uint32_t>> free_bufs;
   // statistics
   std::vector<double> latencies;
   uint64_t bases_done = 0, batches = 0;
@@ -84,6 +86,26 @@ uint64_t rup(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 // Device bytes a request of n bases occupies in a slot (input, staging and output shares).
 uint64_t request_bytes(uint64_t n) { return n / 4 + 24 * n + 64; }
 
+// Run f(0 .. m-1) on up to 8 threads (this one included) when the batch moves enough data
+// (`work` elements) for the threads to pay off; the host copies are what bounds a server.
+template <class F>
+void parallel_for(size_t m, uint64_t work, F f) {
+  unsigned nt = std::thread::hardware_concurrency() / 2;
+  nt = nt < 1 ? 1 : (nt > 8 ? 8 : nt);
+  if (work < (1u << 18) || m < 2 || nt < 2) {
+    for (size_t i = 0; i < m; ++i) f(i);
+    return;
+  }
+  if (nt > m) nt = (unsigned)m;
+  std::vector<std::thread> th;
+  for (unsigned t = 1; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (size_t i = t; i < m; i += nt) f(i);
+    });
+  for (size_t i = 0; i < m; i += nt) f(i);
+  for (auto &x : th) x.join();
+}
+
 void finish_slot(sws_server *s, Slot &sl) {
   // picks of every member: [po[2i], po[2i+1]) -- the odd entries are padding reads
   const uint64_t count = *sl.h_count;
@@ -96,12 +118,27 @@ void finish_slot(sws_server *s, Slot &sl) {
   }
   const int st = sws_batch_sync(sl.bt);
   const Clock::time_point now = Clock::now();
-  std::lock_guard<std::mutex> lock(s->mu);
-  for (size_t i = 0; i < sl.members.size(); ++i) {
-    Request *r = sl.members[i];
+  const size_t m = sl.members.size();
+  // result buffers: reused ones from the pool (short lock), filled without the lock so that
+  // submissions and retrievals proceed meanwhile, then handed to the requests
+  std::vector<std::vector<uint32_t>> bufs(2 * m);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (size_t j = 0; j < 2 * m && !s->free_bufs.empty(); ++j) {
+      bufs[j].swap(s->free_bufs.back());
+      s->free_bufs.pop_back();
+    }
+  }
+  parallel_for(m, sl.h_po[2 * m], [&](size_t i) {
     const uint64_t a = sl.h_po[2 * i], b = sl.h_po[2 * i + 1];
-    r->hash.assign(sl.h_hash + a, sl.h_hash + b);
-    r->pos.assign(sl.h_pos + a, sl.h_pos + b);
+    bufs[2 * i].assign(sl.h_hash + a, sl.h_hash + b);
+    bufs[2 * i + 1].assign(sl.h_pos + a, sl.h_pos + b);
+  });
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (size_t i = 0; i < m; ++i) {
+    Request *r = sl.members[i];
+    r->hash.swap(bufs[2 * i]);
+    r->pos.swap(bufs[2 * i + 1]);
     r->status = st;
     r->done = true;
     r->t_done = now;
@@ -124,12 +161,15 @@ void launch_slot(sws_server *s, Slot &sl) {
   const size_t m = sl.members.size();
   for (size_t i = 0; i < m; ++i) {
     Request *r = sl.members[i];
-    memcpy(sl.h_seq + base / 4, r->seq.data(), r->seq.size());
     sl.h_offs[2 * i] = (int64_t)base;
     sl.h_offs[2 * i + 1] = (int64_t)(base + r->nbases);
     base = rup(base + r->nbases, 4);
   }
   sl.h_offs[2 * m] = (int64_t)base;
+  parallel_for(m, base / 4, [&](size_t i) {
+    const Request *r = sl.members[i];
+    memcpy(sl.h_seq + sl.h_offs[2 * i] / 4, r->seq.data(), r->seq.size());
+  });
   const uint64_t nreads = 2 * m;
   cudaMemcpyAsync(sl.io.seq, sl.h_seq, base / 4, cudaMemcpyHostToDevice, sl.stream);
   cudaMemcpyAsync(sl.io.offsets, sl.h_offs, (nreads + 1) * 8, cudaMemcpyHostToDevice, sl.stream);
@@ -354,6 +394,12 @@ sws_status sws_server_result(sws_server *s, uint64_t request_id, uint32_t *hash,
   }
   const int st = r->status;
   s->reqs.erase(it);
+  if (s->free_bufs.size() < 8192) {  // keep the buffers for later results
+    r->hash.clear();
+    r->pos.clear();
+    s->free_bufs.push_back(std::move(r->hash));
+    s->free_bufs.push_back(std::move(r->pos));
+  }
   delete r;
   return st == SWS_OK ? SWS_OK : sws::report_error(st, "a device-side wait ran out while serving this request");
 }
