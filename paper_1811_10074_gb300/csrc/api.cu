@@ -344,9 +344,9 @@ sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int ki
 struct StagedWs {
   uint64_t counts_off, scan_off, tilebar_off, hash_off, pos_off, first_off, extra_off, total;
 };
-StagedWs staged_ws_layout(uint64_t tiles, int w, int hash_bytes, bool reads, uint64_t extra) {
+StagedWs staged_ws_layout(uint64_t tiles, int tile_windows, int hash_bytes, bool reads, uint64_t extra) {
   StagedWs L;
-  const uint64_t slots = tiles * (uint64_t)sws::mini_fast_tile_windows(w);
+  const uint64_t slots = tiles * (uint64_t)tile_windows;
   L.counts_off = 0;
   L.scan_off = round_up((tiles + 1) * 4, 256);
   L.tilebar_off = L.scan_off + round_up(sws::scan_u32_scratch_words(tiles + 1) * 4, 256);
@@ -364,13 +364,13 @@ sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrie
                           void **extra_ptr, cudaStream_t st) {
   // The staged path (five launches) pays off once the input fills the GPU; below that the
   // single-kernel look-back path has the lower latency.
-  const uint64_t tw = (uint64_t)sws::mini_fast_tile_windows(a.w);
-  const bool staged = sws::mini_fast_applies(source, a.k, a.w) && nwin >= 4 * tw * (uint64_t)ctx->num_sms;
+  const uint64_t tw = (uint64_t)sws::mini_staged_tile_windows(source, a.k, a.w);
+  const bool staged = tw > 0 && nwin >= 4 * tw * (uint64_t)ctx->num_sms;
   if (staged) {
     const uint64_t tiles = (nwin + tw - 1) / tw;
     if (tiles >= 0xffffffffull) return fail(SWS_ERR_INVALID, "input too long");
     const StagedWs L =
-        staged_ws_layout(tiles, a.w, sws::mini_fast_hash_bytes(source, a.k), barrier == sws::BAR_READS, extra);
+        staged_ws_layout(tiles, (int)tw, sws::mini_fast_hash_bytes(source, a.k), barrier == sws::BAR_READS, extra);
     sws_status s = ensure_ws(ctx, L.total, st);
     if (s) return s;
     char *w = static_cast<char *>(ctx->ws);

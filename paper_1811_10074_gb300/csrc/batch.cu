@@ -74,7 +74,7 @@ Layout layout_for(const sws_batch *b, int path) {
   const uint64_t nwin = b->max_bases >= span ? b->max_bases - span + 1 : 0;
   const uint64_t fixb = ((b->max_reads + 1023) / 1024 + 1) * 8;
   if (path == PATH_STAGED) {
-    const uint64_t tw = (uint64_t)sws::mini_fast_tile_windows(b->w);
+    const uint64_t tw = (uint64_t)sws::mini_staged_tile_windows(sws::SRC_DNA, b->k, b->w);
     L.tiles = (nwin + tw - 1) / tw;
     const uint64_t slots = L.tiles * tw;
     L.counts = 0;
@@ -147,7 +147,8 @@ sws_status enqueue(sws_batch *b, int path, cudaStream_t st) {
 void set_desc(sws_batch *b, int path, uint64_t nreads, uint64_t total) {
   const uint64_t span = (uint64_t)(b->w + b->k - 1);
   const uint64_t nwin = (nreads > 0 && total >= span) ? total - span + 1 : 0;
-  const uint64_t tw = (uint64_t)(path == PATH_STAGED ? sws::mini_fast_tile_windows(b->w) : sws::mini_tile_windows(b->w));
+  const uint64_t tw =
+      (uint64_t)(path == PATH_STAGED ? sws::mini_staged_tile_windows(sws::SRC_DNA, b->k, b->w) : sws::mini_tile_windows(b->w));
   const uint64_t tiles = (nwin + tw - 1) / tw;
   memset(b->h_desc, 0, sws::BD_WORDS * 8);
   b->h_desc[sws::BD_NREADS] = nreads;
@@ -257,7 +258,7 @@ sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases
   b->mode = mode;
   b->hash_bytes = 2 * k <= 32 ? 4 : 8;
   b->capacity = max_bases;
-  const bool staged_ok = sws::mini_fast_applies(sws::SRC_DNA, k, w);
+  const bool staged_ok = sws::mini_staged_tile_windows(sws::SRC_DNA, k, w) > 0;  // any w: generic kernel staged
   const uint64_t ws_bytes =
       staged_ok ? (layout_for(b, PATH_STAGED).bytes > layout_for(b, PATH_LOOKBACK).bytes ? layout_for(b, PATH_STAGED).bytes
                                                                                        : layout_for(b, PATH_LOOKBACK).bytes)

@@ -98,6 +98,11 @@ cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrie
 // to a fixed slot, a scan of the per-tile counts gives offsets, a gather puts picks in order.
 bool mini_fast_applies(int source, int k, int w);
 int mini_fast_hash_bytes(int source, int k);  // bytes of a staged key value: 8 when 2k > 32
+// Windows per tile of the staged path: the specialised kernel's for w in 4..16, else the generic
+// kernel's (which then runs in staged mode).
+int mini_staged_tile_windows(int source, int k, int w);
+cudaError_t launch_minimizers_generic_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
+                                             const uint2 *tile_bar, cudaStream_t stream);
 int mini_fast_tile_windows(int w);
 cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
                                      cudaStream_t stream);

@@ -35,22 +35,30 @@ constexpr int MAXB = 128;                 // barriers kept in shared memory per 
 constexpr int STAGE_BYTES_MINI = ((MNT + 6) * 4 + 15) / 16 * 16;
 constexpr int STAGE_BYTES_KMER = ((MNT + 3) * 4 + 15) / 16 * 16;
 // ---- the fused minimizer kernel --------------------------------------------------------------
-template <class KOp, int SRC, int BAR>
+template <class KOp, int SRC, int BAR, bool STAGED>
 struct MiniSmem {
   using BC = BlockCombine<KOp, MNT, MVPT>;
   static constexpr int OFF_BASES = 0;
   static constexpr int OFF_BC = STAGE_BYTES_MINI;
-  static constexpr int OFF_BAR = OFF_BC + ((int)sizeof(typename BC::Shared) + 15) / 16 * 16;
+  // the block-combine buffer, reused for the tile's picks: hash (4 or 8 bytes), position, and in
+  // a staged read batch the read index of a read's first pick
+  static constexpr int PICKS =
+      ML * ((sizeof(typename KeyTraits<KOp>::T) == 8 ? 4 : 8) + 4 + (STAGED && BAR == BAR_READS ? 4 : 0));
+  static constexpr int BC_BYTES = (int)sizeof(typename BC::Shared) > PICKS ? (int)sizeof(typename BC::Shared) : PICKS;
+  static constexpr int OFF_BAR = OFF_BC + (BC_BYTES + 15) / 16 * 16;
   static constexpr int BYTES = OFF_BAR + MAXB * 16;
 };
 
-template <class KOp, int SRC, int BAR>
+// STAGED: instead of ordering its picks by the look-back, a tile writes them to its fixed slot
+// of the staging area with its count (ordered afterwards by a scan and a gather, as the staged
+// kernel of minimizer_fast.cu does); tiles then never wait for one another.
+template <class KOp, int SRC, int BAR, bool STAGED>
 __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span, uint64_t nwin,
                                                     const uint2 *__restrict__ tile_bar) {
   using BC = BlockCombine<KOp, MNT, MVPT>;
   using KT = KeyTraits<KOp>;
   using Key = typename KT::T;
-  using SM = MiniSmem<KOp, SRC, BAR>;
+  using SM = MiniSmem<KOp, SRC, BAR, STAGED>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint8_t *sbases = smem + SM::OFF_BASES;
   typename BC::Shared &sbc = *reinterpret_cast<typename BC::Shared *>(smem + SM::OFF_BC);
@@ -65,15 +73,20 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   __shared__ int s_failed;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
+  if (!STAGED) {
+    if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+  }
+  const uint32_t tile = STAGED ? blockIdx.x : s_tile;
   uint64_t n = a.n;  // bases (or keys)
+  uint32_t num_tiles = gridDim.x;
   if (a.desc) {  // a batch graph launched for the largest batch: sizes of this run
     n = a.desc[BD_TOTAL];
     nwin = a.desc[BD_NWIN];
-    if (tile >= a.desc[BD_TILES]) return;
+    num_tiles = (uint32_t)a.desc[BD_TILES];
+    if (tile >= num_tiles) return;
   }
+  if (STAGED && t == 0 && tile == 0) a.tile_counts[num_tiles] = 0;  // the scan's last entry becomes the total
   const long long p0 = (long long)tile * TW;  // first emitted window of the tile
   const long long ifirst = p0 - 1;             // k-mer / window of local index 0
 
@@ -227,6 +240,40 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   }
   const uint32_t toff = woff + inc - cnt;  // picks of this tile before this thread
 
+  using HashT = typename std::conditional<sizeof(Key) == 8, uint32_t, unsigned long long>::type;
+  HashT *sh_hash = reinterpret_cast<HashT *>(&sbc);
+  uint32_t *sh_pos = reinterpret_cast<uint32_t *>(sh_hash + ML);
+  uint32_t *sh_first = sh_pos + ML;  // staged read batches: read index of a read's first pick
+  if (STAGED) {
+    // stage the tile's picks in order in shared memory, then copy them to the tile's slot
+    __syncthreads();  // the block-combine buffer is reused
+    uint32_t r = toff;
+#pragma unroll
+    for (int j = 0; j < MVPT; ++j) {
+      if ((emask >> j) & 1u) {
+        uint32_t pos = KT::pos(m[j]);
+        if (BAR == BAR_READS) {
+          const uint32_t rd = g_lo + qj[j];
+          pos = (uint32_t)((long long)pos - a.bar[rd]);
+          sh_first[r] = ((firstmask >> j) & 1u) ? rd : 0xFFFFFFFFu;
+        }
+        sh_hash[r] = (HashT)KT::hash(m[j]);
+        sh_pos[r] = pos;
+        ++r;
+      }
+    }
+    __syncthreads();
+    const uint64_t slot = (uint64_t)tile * TW;
+    HashT *gh = static_cast<HashT *>(a.stg_hash);
+    for (uint32_t i = t; i < total; i += MNT) {
+      gh[slot + i] = sh_hash[i];
+      a.stg_pos[slot + i] = sh_pos[i];
+      if (BAR == BAR_READS) a.stg_first[slot + i] = sh_first[i];
+    }
+    if (t == 0) a.tile_counts[tile] = total;
+    return;
+  }
+
   if (warp == 0) {
     bool failed = false;
     const unsigned long long ex = lookback_warp(a.status, tile, total, a.err, failed);
@@ -240,21 +287,16 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   const unsigned long long base = s_excl;
 
   // Stage picks in shared memory (reusing the block-combine buffer), then store coalesced.
-  using HashT = typename std::conditional<sizeof(Key) == 8, uint32_t, unsigned long long>::type;
-  HashT *sh_hash = reinterpret_cast<HashT *>(&sbc);
-  uint32_t *sh_pos = reinterpret_cast<uint32_t *>(sh_hash + ML);
   uint32_t r = toff;
 #pragma unroll
   for (int j = 0; j < MVPT; ++j) {
     if ((emask >> j) & 1u) {
-      const long long p = pf + j;
       uint32_t pos = KT::pos(m[j]);
       if (BAR == BAR_READS) {
         const uint32_t rd = g_lo + qj[j];  // read index of window p
         pos = (uint32_t)((long long)pos - a.bar[rd]);
         if ((firstmask >> j) & 1u) a.pick_offsets[rd] = base + r;
       }
-      (void)p;
       sh_hash[r] = (HashT)KT::hash(m[j]);
       sh_pos[r] = pos;
       ++r;
@@ -421,10 +463,10 @@ __global__ void k_fix_apply(uint64_t *__restrict__ po, uint64_t nreads, const ui
   if (blockIdx.x == 0 && threadIdx.x == 0) po[nreads] = *count;
 }
 
-template <class KOp, int SRC, int BAR>
+template <class KOp, int SRC, int BAR, bool STAGED = false>
 cudaError_t launch_mini_t(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_bar, cudaStream_t st) {
-  using SM = MiniSmem<KOp, SRC, BAR>;
-  auto kern = k_minimizers<KOp, SRC, BAR>;
+  using SM = MiniSmem<KOp, SRC, BAR, STAGED>;
+  auto kern = k_minimizers<KOp, SRC, BAR, STAGED>;
   const size_t sm = SM::BYTES;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -484,6 +526,22 @@ cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrie
   }
   if (wide) return launch_mini_t<OpMinKey96, SRC_DNA, BAR_NBLOCK>(a, num_tiles, tile_bar, st);
   return launch_mini_t<OpMinKey64, SRC_DNA, BAR_NBLOCK>(a, num_tiles, tile_bar, st);
+}
+
+// The generic kernel in staged mode (any w, any k): one CTA per tile of mini_tile_windows(w)
+// windows, picks and counts to the staging area (tile barriers already computed by the caller).
+cudaError_t launch_minimizers_generic_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
+                                             const uint2 *tile_bar, cudaStream_t st) {
+  if (num_tiles == 0) return cudaSuccess;
+  if (num_tiles > 0xffffffffull) return cudaErrorInvalidValue;
+  const bool wide = source == SRC_DNA && 2 * a.k > 32;
+  if (source == SRC_KEYS) return launch_mini_t<OpMinKey64, SRC_KEYS, BAR_NBLOCK, true>(a, num_tiles, nullptr, st);
+  if (barrier == BAR_READS) {
+    if (wide) return launch_mini_t<OpMinKey96, SRC_DNA, BAR_READS, true>(a, num_tiles, tile_bar, st);
+    return launch_mini_t<OpMinKey64, SRC_DNA, BAR_READS, true>(a, num_tiles, tile_bar, st);
+  }
+  if (wide) return launch_mini_t<OpMinKey96, SRC_DNA, BAR_NBLOCK, true>(a, num_tiles, tile_bar, st);
+  return launch_mini_t<OpMinKey64, SRC_DNA, BAR_NBLOCK, true>(a, num_tiles, tile_bar, st);
 }
 
 cudaError_t launch_pick_offsets_fixup(uint64_t *po, uint64_t nreads, const uint64_t *count, uint64_t *scratch,

@@ -491,10 +491,15 @@ int mini_fast_hash_bytes(int source, int k) { return source == SRC_DNA && 2 * k 
 
 int mini_fast_tile_windows(int w) { return w >= 4 && w <= 16 ? (FNT * (16 / w) - 2) * w : 0; }
 
+int mini_staged_tile_windows(int source, int k, int w) {
+  return mini_fast_applies(source, k, w) ? mini_fast_tile_windows(w) : mini_tile_windows(w);
+}
+
 cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, cudaStream_t st) {
   if (num_tiles == 0) return cudaSuccess;
   if (num_tiles >= 0xffffffffull) return cudaErrorInvalidValue;
-  const int TW = mini_fast_tile_windows(a.w);
+  const bool specialised = mini_fast_applies(source, a.k, a.w);
+  const int TW = mini_staged_tile_windows(source, a.k, a.w);
   const int span = source == SRC_DNA ? a.w + a.k - 1 : a.w;
   const uint64_t nwin = a.n >= (uint64_t)span ? a.n - span + 1 : 0;
   cudaError_t e = launch_tile_barriers(a, source, barrier, num_tiles, TW, span, st);
@@ -506,7 +511,8 @@ cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier,
   if (e != cudaSuccess) return e;
   const bool k64 = mini_fast_hash_bytes(source, a.k) == 8;
   using U64 = unsigned long long;
-  if (source == SRC_KEYS) e = launch_bar<BAR_NBLOCK, SRC_KEYS, uint32_t>(a, num_tiles, nullptr, nwin, span, num_sms, st);
+  if (!specialised) e = launch_minimizers_generic_staged(a, source, barrier, num_tiles, tile_bar, st);
+  else if (source == SRC_KEYS) e = launch_bar<BAR_NBLOCK, SRC_KEYS, uint32_t>(a, num_tiles, nullptr, nwin, span, num_sms, st);
   else if (barrier == BAR_READS)
     e = k64 ? launch_bar<BAR_READS, SRC_DNA, U64>(a, num_tiles, tile_bar, nwin, span, num_sms, st)
             : launch_bar<BAR_READS, SRC_DNA, uint32_t>(a, num_tiles, tile_bar, nwin, span, num_sms, st);

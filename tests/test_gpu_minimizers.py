@@ -253,3 +253,28 @@ def test_minimizer_strands(k):
     # positions outside the sequence
     bad = torch.tensor([n - k + 1, n], dtype=torch.int32, device="cuda")
     assert B.minimizer_strands(seq.cuda(), n, k, bad).tolist() == [255, 255]
+
+
+@pytest.mark.parametrize("k,w", [(15, 17), (15, 50), (19, 50), (12, 257), (15, 1000)])
+def test_generic_staged_path(k, w):
+    """Window lengths beyond the specialised kernel, inputs large enough (more than 4 tiles per
+    SM) for the staged path: the generic kernel writes per-tile slots, a scan and a gather order
+    them.  One sequence with and without N-blocks, and a read batch."""
+    rng = np.random.default_rng(k * 1000 + w)
+    n = 3_000_000 + int(rng.integers(1, 5000))
+    seq = synth.acgt_uniform_packed(n, seed=k + w)
+    h, p = B.minimizers(seq.cuda(), n, k, w)
+    rh, rp = oracle.minimizers(seq, n, k, w, deque=True)
+    assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+    iv = random_nblocks(n, rng, 400, 5 * w)
+    nb = torch.from_numpy(iv).cuda()
+    h, p = B.minimizers(seq.cuda(), n, k, w, nblocks=nb)
+    rh, rp = oracle.minimizers(seq, n, k, w, nblocks=iv, deque=True)
+    assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+    lens = rng.integers(0, 6 * w + 200, size=max(3_000_000 // (3 * w + 100), 10))
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    bseq = synth.acgt_uniform_packed(int(offs[-1]), seed=w)
+    bh, bp, bpo = B.minimizers_batch(bseq.cuda(), torch.from_numpy(offs).cuda(), int(offs[-1]), k, w)
+    rh, rp, rpo = oracle.minimizers_batch(bseq, offs, k, w)
+    assert (bpo.cpu().numpy().view(np.uint64) == rpo).all()
+    assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
