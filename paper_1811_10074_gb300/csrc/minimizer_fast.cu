@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 #pragma unroll
         for (int j = 0; j < VPT; ++j) {
           const uint32_t v = key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), a.mode, kmask);
-          x[j] = (j >= jlo && j < jhi) ? (V)v : NONE;
+          x[j] = (V)v;
         }
       } else {
         const uint32_t v2 = __funnelshift_r(sw[q + 2], sw[q + 3], s);
@@ -217,14 +217,19 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
           const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
                                          __funnelshift_r(v0, v1, 2 * j);
           const unsigned long long v = key_value64(kmer64(w64, k, kmask), a.mode, kmask);
-          x[j] = (j >= jlo && j < jhi) ? (V)v : NONE;
+          x[j] = (V)v;
         }
       }
     } else {
       const uint32_t *sk = reinterpret_cast<const uint32_t *>(stage);
       const int r = (int)(i0 - stg.gb0 / 4) + t * VPT;
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) x[j] = (j >= jlo && j < jhi) ? (V)sk[r + j] : NONE;
+      for (int j = 0; j < VPT; ++j) x[j] = (V)sk[r + j];
+    }
+    if (!interior) {  // k-mers outside the sequence never win a window
+#pragma unroll
+      for (int j = 0; j < VPT; ++j)
+        if (j < jlo || j >= jhi) x[j] = NONE;
     }
     // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
     // tile's keys go through shared memory; precomputed keys are read from the stage directly.
@@ -336,21 +341,26 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     }
 
     // ---- windows that store a pick: valid, and the previous window invalid or picked elsewhere ---
+    // windows this tile emits are o in [W, W + TW): all of every thread's but the first's and last's
+    unsigned rmask = (1u << VPT) - 1u;
+    if (t == 0) rmask &= ~((1u << W) - 1u);
+    if (o0 + VPT > W + G::TW) rmask &= (1u << (W + G::TW - o0 > 0 ? W + G::TW - o0 : 0)) - 1u;
     unsigned emask = 0, firstmask = 0;
     {
-      bool pv = pvalid;
+      bool pv = pvalid;  // validity of the window before (not limited to this tile's range)
       uint32_t pp = ypprev;
 #pragma unroll
       for (int j = 0; j < VPT; ++j) {
-        const int o = o0 + j;
         const bool v = (vmask >> j) & 1u;
-        const bool e = v && o >= W && o < W + G::TW && (!pv || yp[j] != pp);
+        const bool e = v && (!pv || yp[j] != pp);
         emask |= (unsigned)e << j;
         firstmask |= (unsigned)(e && !pv) << j;
         pv = v;
         pp = yp[j];
       }
     }
+    emask &= rmask;
+    firstmask &= rmask;
     const uint32_t cnt = __popc(emask);
     uint32_t inc = cnt;
 #pragma unroll
