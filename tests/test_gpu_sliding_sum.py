@@ -204,3 +204,21 @@ def test_tuner_picks_an_applicable_variant_and_auto_uses_it(op, w):
         assert_sampled(op, w, x, y, sample_indices(n - w + 1, np.random.default_rng(w)))
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("op", ["add_i32", "affine_u32", "add_f32"])
+@pytest.mark.parametrize("variant", ["warp", "stream", "auto"])
+def test_streamed_kernels_with_unaligned_output(op, variant):
+    """An aligned input (the tensor copies need it) and an output that starts 4 bytes into its
+    buffer: the streamed kernels fall back to element stores."""
+    n = (1 << 21) + 5
+    x = make_input(op, n, seed=8, device="cuda")
+    for w in (16, 64, 1024):
+        m = n - w + 1
+        buf = torch.empty((m + 1,) + tuple(x.shape[1:]), dtype=x.dtype, device="cuda")
+        y = B.sliding_sum(op, w, x, out=buf[1:], variant=variant)
+        yr = B.sliding_sum(op, w, x, variant="block_combine")
+        torch.cuda.synchronize()
+        if op != "add_f32":
+            assert torch.equal(y, yr), (op, variant, w)
+        assert_sampled(op, w, x, y, sample_indices(m, np.random.default_rng(w)))
