@@ -64,6 +64,7 @@ def parse_args():
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
+    ap.add_argument("--genome-n", type=int, default=3_100_000_000, help="bases of the genome-scale table measurement")
     args = ap.parse_args()
     args.ops = [o for o in args.ops.split(",") if o]
     args.ws = [int(v) for v in args.ws.split(",") if v]
@@ -315,7 +316,7 @@ def run_ours(args, world, rank, local):
                                             f"{dt:.1f} s single-threaded naive O(wN)"}
     if not args.no_extras and rank == 0:
         result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
-        result["genome_table"] = genome_table_extras(dev, ctx)
+        result["genome_table"] = genome_table_extras(dev, ctx, args.genome_n)
         result["batched_reads"] = batch_extras(dev, ctx)
         result["serving"] = serve_extras(ctx)
     del xs, outs
@@ -710,7 +711,7 @@ def main():
             if args.section == "minimizers":
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n)}), flush=True)
             elif args.section == "table":
-                print(json.dumps({"genome_table": genome_table_extras(dev, ctx)}), flush=True)
+                print(json.dumps({"genome_table": genome_table_extras(dev, ctx, args.genome_n)}), flush=True)
             elif args.section == "batch":
                 print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
             else:

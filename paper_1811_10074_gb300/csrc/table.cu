@@ -78,6 +78,22 @@ __device__ __forceinline__ void emit(const PassOut &out, uint64_t i, unsigned lo
 
 __device__ __forceinline__ int digit_of(unsigned long long key, int shift) { return (int)((key >> shift) & 0xFFull); }
 
+// Lanes of the warp holding the same digit as this lane (valid lanes only match valid lanes):
+// one ballot per digit bit.  Ballots issue on the ordinary pipes; __match_any_sync, which computes
+// the same mask, occupies the address-divergence unit for many cycles per call and bounded the
+// scatter kernel.
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid) {
+  const unsigned vb = __ballot_sync(kFull, valid);
+  unsigned peers = valid ? vb : ~vb;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1;
+    const unsigned m = __ballot_sync(kFull, bit);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
+}
+
 // ---- per-tile digit histograms --------------------------------------------------------------
 template <bool WIDE>
 __global__ void __launch_bounds__(RNT) k_radix_hist(PassIn in, uint64_t m, int shift, uint32_t *__restrict__ hist,
@@ -87,16 +103,18 @@ __global__ void __launch_bounds__(RNT) k_radix_hist(PassIn in, uint64_t m, int s
   h[t] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * RTILE;
-#pragma unroll 4
+  // all loads first (the digit needs the key only, not the position of a wide key), then the counts
+  unsigned long long key[RKPT];
+#pragma unroll
   for (int j = 0; j < RKPT; ++j) {
     const uint64_t i = base + (uint64_t)j * RNT + t;
-    if (i < m) {  // the digit needs the key only (not the position of a wide key)
-      const unsigned long long key = in.keys ? in.keys[i]
-                                     : WIDE ? in.hash64[i]
-                                            : (unsigned long long)in.hash32[i] << 32;
-      atomicAdd(&h[digit_of(key, shift)], 1u);
-    }
+    key[j] = 0;
+    if (i < m)
+      key[j] = in.keys ? in.keys[i] : WIDE ? in.hash64[i] : (unsigned long long)in.hash32[i] << 32;
   }
+#pragma unroll
+  for (int j = 0; j < RKPT; ++j)
+    if (base + (uint64_t)j * RNT + t < m) atomicAdd(&h[digit_of(key[j], shift)], 1u);
   __syncthreads();
   hist[(uint64_t)t * ntiles + blockIdx.x] = h[t];
 }
@@ -189,43 +207,51 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(uint32_t *__restrict__ a
 }
 
 // ---- stable scatter ---------------------------------------------------------------------------
+// One CTA per tile.  A wide key's value (the position) is parked in shared memory in input order
+// as soon as it is loaded, so it holds no register while the keys are ranked; the digit and the
+// key's rank within its warp share one register.  (A persistent form that loads the next tile while
+// writing this one out measured slower, and so did 4-byte cp.async copies of the values.)
 template <bool WIDE>
-__global__ void __launch_bounds__(RNT) k_radix_scatter(PassIn in, PassOut out, uint64_t m, int shift,
-                                                       const uint32_t *__restrict__ hist, uint32_t ntiles) {
+__global__ void __launch_bounds__(RNT, 3) k_radix_scatter(PassIn in, PassOut out, uint64_t m, int shift,
+                                                          const uint32_t *__restrict__ hist, uint32_t ntiles) {
   extern __shared__ __align__(16) unsigned char rsm[];
   unsigned long long *s_keys = reinterpret_cast<unsigned long long *>(rsm);          // RTILE
   uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + RTILE);                  // RTILE if WIDE
-  uint32_t(*s_wcnt)[RBINS] = reinterpret_cast<uint32_t(*)[RBINS]>(s_vals + (WIDE ? RTILE : 0));
+  uint32_t *s_vraw = s_vals + (WIDE ? RTILE : 0);                                   // RTILE if WIDE
+  uint32_t(*s_wcnt)[RBINS] = reinterpret_cast<uint32_t(*)[RBINS]>(s_vraw + (WIDE ? RTILE : 0));
   __shared__ uint32_t s_tstart[RBINS];  // tile-local start of each digit
-  __shared__ uint32_t s_gofs[RBINS];    // global start of each digit for this tile
+  __shared__ uint32_t s_delta[RBINS];   // global start of each digit for this tile - s_tstart
   __shared__ uint32_t s_wsum[RWARPS];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint64_t base = (uint64_t)blockIdx.x * RTILE;
   const uint64_t wbase = base + (uint64_t)warp * (RKPT * 32);
+  const int wslot = warp * (RKPT * 32) + lane;  // s_vraw slot of key j: wslot + 32 j
 
   for (int i = t; i < RWARPS * RBINS; i += RNT) (&s_wcnt[0][0])[i] = 0;
   __syncthreads();
 
   unsigned long long key[RKPT];
-  uint32_t val[RKPT];
-  uint32_t rank[RKPT];
-  int dig[RKPT];
+  uint32_t rd[RKPT];  // digit << 16 | rank within the warp (ranks < 512; digit RBINS past the end)
 #pragma unroll
   for (int j = 0; j < RKPT; ++j) {
     const uint64_t i = wbase + (uint64_t)j * 32 + lane;
-    val[j] = 0;
     key[j] = 0;
-    dig[j] = RBINS;  // out of range: its own peer group, never written
+    rd[j] = (uint32_t)RBINS << 16;  // out of range: its own peer group, never written
     if (i < m) {
-      fetch<WIDE>(in, i, key[j], val[j]);
-      dig[j] = digit_of(key[j], shift);
+      if (WIDE) {
+        key[j] = in.keys ? in.keys[i] : in.hash64[i];
+        s_vraw[wslot + 32 * j] = in.keys ? in.vals[i] : in.pos[i];
+      } else {
+        key[j] = in.keys ? in.keys[i] : ((unsigned long long)in.hash32[i] << 32) | in.pos[i];
+      }
+      rd[j] = (uint32_t)digit_of(key[j], shift) << 16;
     }
   }
   // stable ranks within the warp's 512 keys, in index order (j, then lane)
 #pragma unroll
   for (int j = 0; j < RKPT; ++j) {
-    const int d = dig[j];
-    const unsigned peers = __match_any_sync(kFull, d);
+    const int d = (int)(rd[j] >> 16);
+    const unsigned peers = digit_peers(d, d < RBINS);
     const int leader = __ffs(peers) - 1;
     const uint32_t before = __popc(peers & lanemask_lt(lane));
     uint32_t b = 0;
@@ -234,7 +260,7 @@ __global__ void __launch_bounds__(RNT) k_radix_scatter(PassIn in, PassOut out, u
       s_wcnt[warp][d] = b + (uint32_t)__popc(peers);
     }
     b = __shfl_sync(kFull, b, leader);
-    rank[j] = b + before;
+    rd[j] |= b + before;
     __syncwarp();
   }
   __syncthreads();
@@ -252,20 +278,22 @@ __global__ void __launch_bounds__(RNT) k_radix_scatter(PassIn in, PassOut out, u
       if (lane >= d) inc += u;
     }
     if (lane == 31) s_wsum[warp] = inc;
-    s_gofs[t] = hist[(uint64_t)t * ntiles + blockIdx.x];
+    s_delta[t] = hist[(uint64_t)t * ntiles + blockIdx.x];  // the digit's global start, for now
     __syncthreads();
     uint32_t off = 0;
     for (int k = 0; k < warp; ++k) off += s_wsum[k];
-    s_tstart[t] = off + inc - run;
+    const uint32_t tstart = off + inc - run;
+    s_tstart[t] = tstart;
+    s_delta[t] -= tstart;  // >= 0: the tile's keys of smaller digits all precede the global start
   }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < RKPT; ++j) {
-    const int d = dig[j];
+    const int d = (int)(rd[j] >> 16);
     if (d < RBINS) {
-      const uint32_t idx = s_tstart[d] + s_wcnt[warp][d] + rank[j];
+      const uint32_t idx = s_tstart[d] + s_wcnt[warp][d] + (rd[j] & 0xFFFFu);
       s_keys[idx] = key[j];
-      if (WIDE) s_vals[idx] = val[j];
+      if (WIDE) s_vals[idx] = s_vraw[wslot + 32 * j];
     }
   }
   __syncthreads();
@@ -273,8 +301,7 @@ __global__ void __launch_bounds__(RNT) k_radix_scatter(PassIn in, PassOut out, u
   const uint32_t cnt = left < (uint64_t)RTILE ? (uint32_t)left : (uint32_t)RTILE;
   for (uint32_t i = t; i < cnt; i += RNT) {
     const unsigned long long k = s_keys[i];
-    const int d = digit_of(k, shift);
-    const uint64_t dst = (uint64_t)s_gofs[d] + (i - s_tstart[d]);
+    const uint64_t dst = (uint64_t)s_delta[digit_of(k, shift)] + i;
     emit<WIDE>(out, dst, k, s_vals[WIDE ? i : 0]);
   }
 }
@@ -350,7 +377,7 @@ cudaError_t sort_t(const TableArgs &a, cudaStream_t st) {
     k_radix_hist<WIDE><<<ntiles, RNT, 0, st>>>(in, m, shift, a.ws_hist, ntiles);
     cudaError_t e = scan_u32(a.ws_hist, (uint64_t)RBINS * ntiles, a.ws_bsum, st);
     if (e != cudaSuccess) return e;
-    const size_t sm = (size_t)RTILE * (8 + (WIDE ? 4 : 0)) + (size_t)RWARPS * RBINS * 4;
+    const size_t sm = (size_t)RTILE * (8 + (WIDE ? 8 : 0)) + (size_t)RWARPS * RBINS * 4;
     if (p == 0 && sm > 48 * 1024) {
       e = cudaFuncSetAttribute(k_radix_scatter<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
