@@ -94,11 +94,12 @@ int mini_tile_windows(int w);  // windows per tile (a multiple of 64), 0 if w is
 uint64_t mini_lookback_tiles(uint64_t nwin, int w);
 cudaError_t launch_minimizers_lookback(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
                                        cudaStream_t stream);
-// Staged path (w in 4..16, keys of at most 32 bits): a persistent kernel writes each tile's picks
-// to a fixed slot, a scan of the per-tile counts gives offsets, a gather puts picks in order.
+// Staged path (w in 4..256, k-mers of at most 32 bases or precomputed keys): a persistent kernel
+// writes each tile's picks to a fixed slot, a scan of the per-tile counts gives offsets, a gather
+// puts picks in order.
 bool mini_fast_applies(int source, int k, int w);
 int mini_fast_hash_bytes(int source, int k);  // bytes of a staged key value: 8 when 2k > 32
-// Windows per tile of the staged path: the specialised kernel's for w in 4..16, else the generic
+// Windows per tile of the staged path: the specialised kernel's for w in 4..256, else the generic
 // kernel's (which then runs in staged mode).
 int mini_staged_tile_windows(int source, int k, int w);
 cudaError_t launch_minimizers_generic_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,

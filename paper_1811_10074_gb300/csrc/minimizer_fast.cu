@@ -1,4 +1,4 @@
-// minimizer_fast.cu -- minimizers for window lengths w = 4..16 (any k <= 32, or precomputed
+// minimizer_fast.cu -- minimizers for window lengths w = 4..256 (any k <= 32, or precomputed
 // 32-bit keys), in three steps that never wait on one another inside a kernel:
 //
 //   1. k_mini_stage (persistent, one CTA per resident slot, tiles assigned statically): keys of a
@@ -13,10 +13,14 @@
 // (the single-kernel path in minimizer.cu orders its output with a look-back instead).
 //
 // Details of step 1:
-// * A tile starts at a multiple of w and a thread owns VPT = w * floor(16 / w) consecutive k-mers,
-//   so the blocks of w are whole, compile-time groups of registers: the block-combine (in-block
-//   suffix minimum with the next block's prefix minimum) needs no segment bookkeeping and runs on
-//   the key values themselves (32-bit for 2k <= 32 and precomputed keys, 64-bit otherwise).
+// * w <= 16: a tile starts at a multiple of w and a thread owns VPT = w * floor(16 / w) consecutive
+//   k-mers, so the blocks of w are whole, compile-time groups of registers: the block-combine
+//   (in-block suffix minimum with the next block's prefix minimum) needs no segment bookkeeping and
+//   runs on the key values themselves (32-bit for 2k <= 32 and precomputed keys, 64-bit otherwise).
+// * 16 < w <= 256 (w known at run time): a thread's 16 k-mers are a chunk; with chunk prefix and
+//   suffix minima and chunk minima in shared memory, window o is the suffix minimum at o, the
+//   minima of the whole chunks it covers, and the prefix minimum at o + w - 1 (Eq. 2 combined over
+//   blocks shorter than w): still O(1) per window for a fixed w, with no segmented scan.
 // * Ties.  Keys are ordered by (value, position).  Instead of 64-bit keys, the scans carry a 32-bit
 //   value and the position of its leftmost occurrence: a prefix step takes the new element only
 //   when strictly smaller, a suffix step when smaller or equal, and a window's suffix part (left)
@@ -39,18 +43,37 @@ constexpr int FNT = 256;
 constexpr int FNW = FNT / 32;
 constexpr int FMAXB = 128;
 
+// W = 4..16: blocks of w whole in each thread's registers.  W = 0 (CHUNK): any w in 17..CHUNK_MAXW
+// given at run time; each thread's 16 k-mers form a chunk, and a window is the suffix of its first
+// chunk, whole chunks, and a prefix of its last chunk.
+constexpr int CHUNK = 0;
+constexpr int CHUNK_VPT = 16;
+constexpr int CHUNK_MAXW = 256;
+__host__ __device__ constexpr int chunk_tile_windows(int w) {  // TW <= L - 2w + 1, a multiple of 16
+  return (FNT * CHUNK_VPT - 2 * w + 1) / 16 * 16;
+}
+
 template <int W, int SRC, int BAR, class V>
 struct Geo {
-  static constexpr int NB = 16 / W;              // blocks of w per thread
-  static constexpr int VPT = W * NB;             // k-mers per thread
-  static constexpr int L = FNT * VPT;            // k-mers per tile
-  static constexpr int TW = (FNT * NB - 2) * W;  // windows per tile (a multiple of w)
+  static constexpr bool CH = W == CHUNK;
+  static constexpr int NB = CH ? 1 : 16 / W;              // blocks of w per thread
+  static constexpr int VPT = CH ? CHUNK_VPT : W * NB;     // k-mers per thread
+  static constexpr int L = FNT * VPT;                     // k-mers per tile
+  static constexpr int TW = CH ? L : (FNT * NB - 2) * W;  // windows per tile (CH: an upper bound)
   static constexpr int STAGE = SRC == SRC_DNA ? ((63 + L + 16) / 4 + 16 + 15) / 16 * 16 : (L + 8) * 4;
-  static constexpr int OFF_SX = 2 * STAGE;  // DNA: keys of the tile, sx[o + 1] (keys: read from the stage)
-  static constexpr int OFF_BAR = OFF_SX + (SRC == SRC_DNA ? ((L + 2) * (int)sizeof(V) + 15) / 16 * 16 : 0);
-  static constexpr int OFF_PICKS = OFF_BAR + FMAXB * 16;
   // picks: value (V), position, and for read batches the read index of a read's first pick
-  static constexpr int BYTES = OFF_PICKS + TW * ((int)sizeof(V) + (BAR == BAR_READS ? 8 : 4));
+  static constexpr int PICK_BYTES = TW * ((int)sizeof(V) + (BAR == BAR_READS ? 8 : 4));
+  // CH: chunk prefix minima (value, position) at padded index o + o/16, then per chunk its minimum
+  // (value, position) and last key; they are dead once the windows are known, and the picks reuse
+  // the space.  Otherwise, DNA: keys of the tile, sx[o + 1] (keys: read from the stage).
+  static constexpr int LP = L + L / 16;
+  static constexpr int CH_BYTES = LP * ((int)sizeof(V) + 4) + FNT * (2 * (int)sizeof(V) + 4);
+  static constexpr int SX_BYTES = CH ? (CH_BYTES > PICK_BYTES ? CH_BYTES : PICK_BYTES)
+                                     : (SRC == SRC_DNA ? (L + 2) * (int)sizeof(V) : 0);
+  static constexpr int OFF_SX = 2 * STAGE;
+  static constexpr int OFF_BAR = OFF_SX + (SX_BYTES + 15) / 16 * 16;
+  static constexpr int OFF_PICKS = CH ? OFF_SX : OFF_BAR + FMAXB * 16;
+  static constexpr int BYTES = CH ? OFF_BAR + FMAXB * 16 : OFF_PICKS + PICK_BYTES;
 };
 
 __device__ __forceinline__ long long floor_div(long long a, long long b) {
@@ -69,6 +92,8 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
   using G = Geo<W, SRC, BAR, V>;
   constexpr V NONE = ~(V)0;
   constexpr int VPT = G::VPT, NB = G::NB, WM1 = W > 1 ? W - 1 : 1;
+  const int w = G::CH ? a.w : W;                              // window length
+  const int TW = G::CH ? chunk_tile_windows(a.w) : G::TW;     // windows per tile
   extern __shared__ __align__(16) unsigned char smem[];
   V *sx = reinterpret_cast<V *>(smem + G::OFF_SX);
   long long *sbar = reinterpret_cast<long long *>(smem + G::OFF_BAR);
@@ -92,7 +117,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 
   // Thread 0: start the bulk copy of tile `tile`'s bases (or keys) into buffer b.
   auto issue = [&](int b, uint32_t tile) {
-    const long long i0 = (long long)tile * G::TW - W;
+    const long long i0 = (long long)tile * TW - w;
     const long long gb0 = SRC == SRC_DNA ? floor_div(i0, 64) * 16 : floor_div(i0, 4) * 16;
     const long long lo = gb0 > 0 ? gb0 : 0;
     long long hi = gb0 + G::STAGE;
@@ -120,8 +145,8 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
   for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
     const int b = it & 1;
     if (t == 0 && tile + gridDim.x < num_tiles) issue(b ^ 1, tile + gridDim.x);
-    const long long p0 = (long long)tile * G::TW;  // first window of the tile
-    const long long i0 = p0 - W;                   // k-mer (and window) of local index 0
+    const long long p0 = (long long)tile * TW;  // first window of the tile
+    const long long i0 = p0 - w;                // k-mer (and window) of local index 0
     uint8_t *stage = smem + b * G::STAGE;
 
     // ---- bases (or keys) of this tile in shared memory; barriers that can touch it ------------
@@ -189,7 +214,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 
     // ---- keys (32-bit values) ------------------------------------------------------------------
     const long long ifirst = i0 + (long long)t * VPT;
-    const long long tlo = p0 - 1, thi = p0 + G::TW - 1;  // windows this tile looks at
+    const long long tlo = p0 - 1, thi = p0 + TW - 1;  // windows this tile looks at
     const bool interior = nb == 0 && tlo >= 0 && (unsigned long long)thi < nwin;
     const long long lastv = (long long)n - (SRC == SRC_DNA ? a.k : 1);  // last valid k-mer
     const int jlo = interior ? 0 : (ifirst < 0 ? (int)(-ifirst < VPT ? -ifirst : VPT) : 0);
@@ -231,77 +256,187 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       for (int j = 0; j < VPT; ++j)
         if (j < jlo || j >= jhi) x[j] = NONE;
     }
-    // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
-    // tile's keys go through shared memory; precomputed keys are read from the stage directly.
-    const V *kx;  // kx[o]: key of tile-local k-mer o
-    if (SRC == SRC_DNA) {
-#pragma unroll
-      for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
-      __syncthreads();
-      kx = sx + 1;
-    } else {
-      kx = reinterpret_cast<const V *>(stage) + (i0 - stg.gb0 / 4);  // V is 32-bit for precomputed keys
-    }
-
-    // ---- window minima and their leftmost positions, by block-combine on registers -----------
-    // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
-    // on ties (strict <), suffix minima the earliest too (<=); a window's suffix part lies left of
-    // its prefix part, so ties between the two go to the suffix.
-    V xn[WM1];  // the next thread's first w-1 keys
-#pragma unroll
-    for (int i = 0; i < W - 1; ++i) xn[i] = kx[(t + 1 < FNT ? t + 1 : t) * VPT + i];
-    const V xprev = t > 0 ? kx[t * VPT - 1] : NONE;  // key of k-mer ifirst - 1 (unused for thread 0)
     const int o0 = t * VPT;
-    V P[VPT], S[VPT], Pn[WM1], y[VPT];
-    uint32_t Pp[VPT], Sp[VPT], Pnp[WM1], yp[VPT];
+    V y[VPT];
+    uint32_t yp[VPT];
+    uint32_t ypprev;  // pick of the window just before this thread's first (tile-local position)
+    if constexpr (!G::CH) {
+      // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
+      // tile's keys go through shared memory; precomputed keys are read from the stage directly.
+      const V *kx;  // kx[o]: key of tile-local k-mer o
+      if (SRC == SRC_DNA) {
 #pragma unroll
-    for (int b2 = 0; b2 < NB; ++b2) {
-      P[b2 * W] = x[b2 * W];
-      Pp[b2 * W] = o0 + b2 * W;
+        for (int j = 0; j < VPT; ++j) sx[1 + t * VPT + j] = x[j];
+        __syncthreads();
+        kx = sx + 1;
+      } else {
+        kx = reinterpret_cast<const V *>(stage) + (i0 - stg.gb0 / 4);  // V is 32-bit for precomputed keys
+      }
+
+      // ---- window minima and their leftmost positions, by block-combine on registers -----------
+      // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
+      // on ties (strict <), suffix minima the earliest too (<=); a window's suffix part lies left of
+      // its prefix part, so ties between the two go to the suffix.
+      V xn[WM1];  // the next thread's first w-1 keys
 #pragma unroll
-      for (int i = 1; i < W; ++i) {
-        const int j = b2 * W + i;
+      for (int i = 0; i < W - 1; ++i) xn[i] = kx[(t + 1 < FNT ? t + 1 : t) * VPT + i];
+      const V xprev = t > 0 ? kx[t * VPT - 1] : NONE;  // key of k-mer ifirst - 1 (unused for thread 0)
+      V P[VPT], S[VPT], Pn[WM1];
+      uint32_t Pp[VPT], Sp[VPT], Pnp[WM1];
+#pragma unroll
+      for (int b2 = 0; b2 < NB; ++b2) {
+        P[b2 * W] = x[b2 * W];
+        Pp[b2 * W] = o0 + b2 * W;
+#pragma unroll
+        for (int i = 1; i < W; ++i) {
+          const int j = b2 * W + i;
+          const bool c = x[j] < P[j - 1];
+          P[j] = c ? x[j] : P[j - 1];
+          Pp[j] = c ? (uint32_t)(o0 + j) : Pp[j - 1];
+        }
+        S[b2 * W + W - 1] = x[b2 * W + W - 1];
+        Sp[b2 * W + W - 1] = o0 + b2 * W + W - 1;
+#pragma unroll
+        for (int i = W - 2; i >= 0; --i) {
+          const int j = b2 * W + i;
+          const bool c = x[j] <= S[j + 1];
+          S[j] = c ? x[j] : S[j + 1];
+          Sp[j] = c ? (uint32_t)(o0 + j) : Sp[j + 1];
+        }
+      }
+      if (W > 1) {
+        Pn[0] = xn[0];
+        Pnp[0] = o0 + VPT;
+#pragma unroll
+        for (int i = 1; i < W - 1; ++i) {
+          const bool c = xn[i] < Pn[i - 1];
+          Pn[i] = c ? xn[i] : Pn[i - 1];
+          Pnp[i] = c ? (uint32_t)(o0 + VPT + i) : Pnp[i - 1];
+        }
+      }
+#pragma unroll
+      for (int b2 = 0; b2 < NB; ++b2) {
+        y[b2 * W] = S[b2 * W];
+        yp[b2 * W] = Sp[b2 * W];
+#pragma unroll
+        for (int i = 1; i < W; ++i) {
+          const int j = b2 * W + i;
+          const V pr = (b2 + 1 < NB) ? P[(b2 + 1) * W + i - 1] : Pn[i - 1];
+          const uint32_t prp = (b2 + 1 < NB) ? Pp[(b2 + 1) * W + i - 1] : Pnp[i - 1];
+          const bool c = S[j] <= pr;
+          y[j] = c ? S[j] : pr;
+          yp[j] = c ? Sp[j] : prp;
+        }
+      }
+      // pick of the window just before this thread's first: k-mer ifirst-1 and this block's first w-1
+      ypprev = W > 1 ? (xprev <= P[W > 1 ? W - 2 : 0] ? (uint32_t)(o0 - 1) : Pp[W > 1 ? W - 2 : 0])
+                                    : (uint32_t)(o0 - 1);
+    } else {
+      // ---- chunks of 16 k-mers: window [o, o + w - 1] = suffix of o's chunk, the whole chunks
+      // between, and a prefix of the chunk holding o + w - 1 (Eq. 2 with blocks shorter than w).
+      // Ties: prefix minima keep the earliest position (strict <), suffix minima too (<=), and each
+      // later piece replaces the running minimum only when strictly smaller.
+      V *cPv = reinterpret_cast<V *>(smem + G::OFF_SX);        // [LP] chunk prefix minima
+      uint32_t *cPp = reinterpret_cast<uint32_t *>(cPv + G::LP);  // [LP] their positions
+      V *cTv = reinterpret_cast<V *>(cPp + G::LP);              // [FNT] chunk minima
+      V *cLast = cTv + FNT;                                      // [FNT] each chunk's last key
+      uint32_t *cTp = reinterpret_cast<uint32_t *>(cLast + FNT);  // [FNT] chunk minima positions
+      auto pad = [](int o) { return o + (o >> 4); };              // conflict-free strided access
+      V P[VPT], S[VPT];
+      uint32_t Pp[VPT], Sp[VPT];
+      P[0] = x[0];
+      Pp[0] = o0;
+#pragma unroll
+      for (int j = 1; j < VPT; ++j) {
         const bool c = x[j] < P[j - 1];
         P[j] = c ? x[j] : P[j - 1];
         Pp[j] = c ? (uint32_t)(o0 + j) : Pp[j - 1];
       }
-      S[b2 * W + W - 1] = x[b2 * W + W - 1];
-      Sp[b2 * W + W - 1] = o0 + b2 * W + W - 1;
+      S[VPT - 1] = x[VPT - 1];
+      Sp[VPT - 1] = o0 + VPT - 1;
 #pragma unroll
-      for (int i = W - 2; i >= 0; --i) {
-        const int j = b2 * W + i;
+      for (int j = VPT - 2; j >= 0; --j) {
         const bool c = x[j] <= S[j + 1];
         S[j] = c ? x[j] : S[j + 1];
         Sp[j] = c ? (uint32_t)(o0 + j) : Sp[j + 1];
       }
-    }
-    if (W > 1) {
-      Pn[0] = xn[0];
-      Pnp[0] = o0 + VPT;
 #pragma unroll
-      for (int i = 1; i < W - 1; ++i) {
-        const bool c = xn[i] < Pn[i - 1];
-        Pn[i] = c ? xn[i] : Pn[i - 1];
-        Pnp[i] = c ? (uint32_t)(o0 + VPT + i) : Pnp[i - 1];
+      for (int j = 0; j < VPT; ++j) {
+        cPv[pad(o0 + j)] = P[j];
+        cPp[pad(o0 + j)] = Pp[j];
       }
-    }
-#pragma unroll
-    for (int b2 = 0; b2 < NB; ++b2) {
-      y[b2 * W] = S[b2 * W];
-      yp[b2 * W] = Sp[b2 * W];
-#pragma unroll
-      for (int i = 1; i < W; ++i) {
-        const int j = b2 * W + i;
-        const V pr = (b2 + 1 < NB) ? P[(b2 + 1) * W + i - 1] : Pn[i - 1];
-        const uint32_t prp = (b2 + 1 < NB) ? Pp[(b2 + 1) * W + i - 1] : Pnp[i - 1];
-        const bool c = S[j] <= pr;
-        y[j] = c ? S[j] : pr;
-        yp[j] = c ? Sp[j] : prp;
+      cTv[t] = S[0];
+      cTp[t] = Sp[0];
+      cLast[t] = x[VPT - 1];
+      __syncthreads();
+      // w - 1 = 16 A + c: window o0 + j ends in chunk t + A (j + c < 16) or t + A + 1; the window
+      // [o0, o0 + w - 2] before it ends in chunk t + B, B = (w - 2) / 16.
+      const int A = (w - 1) >> 4, c = (w - 1) & 15, B = (w - 2) >> 4;
+      V M0 = NONE, Mb = NONE;  // minima of chunks t+1 .. t+A-1 and t+1 .. t+B-1
+      uint32_t M0p = 0, Mbp = 0;
+      for (int i = 1; i < A; ++i) {
+        if (i == B) {
+          Mb = M0;
+          Mbp = M0p;
+        }
+        const int u = t + i < FNT ? t + i : FNT - 1;  // past the tile: windows this tile does not emit
+        const V v = cTv[u];
+        if (v < M0) {
+          M0 = v;
+          M0p = cTp[u];
+        }
       }
+      if (B == A) {
+        Mb = M0;
+        Mbp = M0p;
+      }
+      V M1 = M0;  // chunks t+1 .. t+A
+      uint32_t M1p = M0p;
+      {
+        const int u = t + A < FNT ? t + A : FNT - 1;
+        const V v = cTv[u];
+        if (v < M1) {
+          M1 = v;
+          M1p = cTp[u];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        const int q = o0 + j + w - 1 < G::L ? o0 + j + w - 1 : G::L - 1;
+        const bool far = j + c >= 16;
+        V acc = S[j];
+        uint32_t accp = Sp[j];
+        const V m = far ? M1 : M0;
+        if (m < acc) {
+          acc = m;
+          accp = far ? M1p : M0p;
+        }
+        const V pv = cPv[pad(q)];
+        if (pv < acc) {
+          acc = pv;
+          accp = cPp[pad(q)];
+        }
+        y[j] = acc;
+        yp[j] = accp;
+      }
+      // the window before: k-mer o0 - 1, then [o0, o0 + w - 2] (the whole chunk when w = 17)
+      V part = S[0];
+      uint32_t partp = Sp[0];
+      if (B > 0) {
+        if (Mb < part) {
+          part = Mb;
+          partp = Mbp;
+        }
+        const int q = o0 + w - 2 < G::L ? o0 + w - 2 : G::L - 1;
+        const V pv = cPv[pad(q)];
+        if (pv < part) {
+          part = pv;
+          partp = cPp[pad(q)];
+        }
+      }
+      const V xprev = t > 0 ? cLast[t - 1] : NONE;
+      ypprev = xprev <= part ? (uint32_t)(o0 - 1) : partp;
     }
-    // pick of the window just before this thread's first: k-mer ifirst-1 and this block's first w-1
-    const uint32_t ypprev = W > 1 ? (xprev <= P[W > 1 ? W - 2 : 0] ? (uint32_t)(o0 - 1) : Pp[W > 1 ? W - 2 : 0])
-                                  : (uint32_t)(o0 - 1);
 
     // ---- window validity -------------------------------------------------------------------------
     unsigned vmask;
@@ -341,10 +476,10 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     }
 
     // ---- windows that store a pick: valid, and the previous window invalid or picked elsewhere ---
-    // windows this tile emits are o in [W, W + TW): all of every thread's but the first's and last's
+    // windows this tile emits are o in [w, w + TW): all but those of the first and last threads
     unsigned rmask = (1u << VPT) - 1u;
-    if (t == 0) rmask &= ~((1u << W) - 1u);
-    if (o0 + VPT > W + G::TW) rmask &= (1u << (W + G::TW - o0 > 0 ? W + G::TW - o0 : 0)) - 1u;
+    if (o0 < w) rmask &= ~((1u << (w - o0 < VPT ? w - o0 : VPT)) - 1u);
+    if (o0 + VPT > w + TW) rmask &= (1u << (w + TW - o0 > 0 ? w + TW - o0 : 0)) - 1u;
     unsigned emask = 0, firstmask = 0;
     {
       bool pv = pvalid;  // validity of the window before (not limited to this tile's range)
@@ -395,7 +530,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       }
     }
     __syncthreads();
-    const uint64_t slot = (uint64_t)tile * G::TW;
+    const uint64_t slot = (uint64_t)tile * TW;
     for (uint32_t i = t; i < total; i += FNT) {
       static_cast<V *>(a.stg_hash)[slot + i] = sh_hash[i];
       a.stg_pos[slot + i] = sh_pos[i];
@@ -487,19 +622,24 @@ cudaError_t launch_bar(const MiniArgs &a, uint64_t num_tiles, const uint2 *tile_
     case 14: return launch_w<14, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
     case 15: return launch_w<15, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
     case 16: return launch_w<16, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
-    default: return cudaErrorNotSupported;
+    default:
+      if (a.w > 16 && a.w <= CHUNK_MAXW) return launch_w<CHUNK, BAR, SRC, V>(a, num_tiles, tile_bar, nwin, span, num_sms, st);
+      return cudaErrorNotSupported;
   }
 }
 
 }  // namespace
 
 bool mini_fast_applies(int source, int k, int w) {
-  return w >= 4 && w <= 16 && (source == SRC_KEYS || (k >= 1 && k <= 32));
+  return w >= 4 && w <= CHUNK_MAXW && (source == SRC_KEYS || (k >= 1 && k <= 32));
 }
 
 int mini_fast_hash_bytes(int source, int k) { return source == SRC_DNA && 2 * k > 32 ? 8 : 4; }
 
-int mini_fast_tile_windows(int w) { return w >= 4 && w <= 16 ? (FNT * (16 / w) - 2) * w : 0; }
+int mini_fast_tile_windows(int w) {
+  if (w >= 4 && w <= 16) return (FNT * (16 / w) - 2) * w;
+  return w > 16 && w <= CHUNK_MAXW ? chunk_tile_windows(w) : 0;
+}
 
 int mini_staged_tile_windows(int source, int k, int w) {
   return mini_fast_applies(source, k, w) ? mini_fast_tile_windows(w) : mini_tile_windows(w);

@@ -255,11 +255,47 @@ def test_minimizer_strands(k):
     assert B.minimizer_strands(seq.cuda(), n, k, bad).tolist() == [255, 255]
 
 
+# Window lengths 17..256 of the staged kernel's chunked form (w at run time; a window is the
+# suffix of its first 16-k-mer chunk, whole chunks, and a prefix of its last chunk).  Inputs of
+# 700 tiles take the staged path, more than 4 tiles per SM on a 152-SM GB300.
+CHUNK_WS = [17, 18, 31, 32, 33, 47, 48, 49, 50, 63, 64, 65, 100, 128, 200, 255, 256]
+
+
+@pytest.mark.parametrize("w", CHUNK_WS)
+def test_chunked_window_lengths(w):
+    rng = np.random.default_rng(5000 + w)
+    tw = (4096 - 2 * w + 1) // 16 * 16
+    combos = [(15, "hash"), (19, "hash"), (32, "canonical"), (5, "fwd"), (16, "canonical"), (17, "fwd")]
+    for k, mode in combos[w % 2::2]:
+        n = 700 * tw + int(rng.integers(1, tw))
+        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+        check_minimizers(seq, n, k, w, mode)
+        iv = random_nblocks(n, rng, 300, 3 * w)
+        check_minimizers(seq, n, k, w, mode, iv)
+    m = 700 * tw + 13
+    for name, k64 in (("few values", rng.integers(0, 3, size=m, dtype=np.int64)),
+                      ("sawtooth", np.arange(m, dtype=np.int64) % (3 * w + 1)),
+                      ("decreasing", np.arange(m, 0, -1, dtype=np.int64)),
+                      ("full range", rng.integers(0, 1 << 32, size=m, dtype=np.int64))):
+        keys = k64.astype(np.uint32)
+        h, p = B.minimizers_from_keys(torch.from_numpy(keys.view(np.int32)).cuda(), w)
+        rh, rp = oracle.minimizers_from_keys(keys.astype(np.uint64), w)
+        assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all(), (w, name)
+    lens = rng.integers(0, 6 * w + 200, size=3_000_000 // (3 * w + 100))
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    bseq = synth.acgt_uniform_packed(int(offs[-1]), seed=w)
+    bh, bp, bpo = B.minimizers_batch(bseq.cuda(), torch.from_numpy(offs).cuda(), int(offs[-1]), 15, w)
+    rh, rp, rpo = oracle.minimizers_batch(bseq, offs, 15, w)
+    assert (bpo.cpu().numpy().view(np.uint64) == rpo).all()
+    assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
+
+
 @pytest.mark.parametrize("k,w", [(15, 17), (15, 50), (19, 50), (12, 257), (15, 1000)])
 def test_generic_staged_path(k, w):
-    """Window lengths beyond the specialised kernel, inputs large enough (more than 4 tiles per
-    SM) for the staged path: the generic kernel writes per-tile slots, a scan and a gather order
-    them.  One sequence with and without N-blocks, and a read batch."""
+    """Window lengths beyond the w <= 16 kernel, inputs large enough (more than 4 tiles per SM)
+    for the staged path: the chunked form of the staged kernel up to w = 256, the generic kernel
+    (per-tile slots, then a scan and a gather) beyond.  One sequence with and without N-blocks,
+    and a read batch."""
     rng = np.random.default_rng(k * 1000 + w)
     n = 3_000_000 + int(rng.integers(1, 5000))
     seq = synth.acgt_uniform_packed(n, seed=k + w)
