@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     const int o0 = t * VPT;
     V y[VPT];
     uint32_t yp[VPT];
-    uint32_t ypprev;  // pick of the window just before this thread's first (tile-local position)
+    uint32_t ypprev;  // pick of the window just before this thread's first
+    // positions in y/yp/ypprev are tile-local (chunked form) or offsets from o0 (register form)
+    const uint32_t pos_base = (uint32_t)i0 + (G::CH ? 0u : (uint32_t)o0);
     if constexpr (!G::CH) {
       // DNA: every thread needs the next thread's first w-1 keys and the key before its own, so the
       // tile's keys go through shared memory; precomputed keys are read from the stage directly.
@@ -274,7 +276,8 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       }
 
       // ---- window minima and their leftmost positions, by block-combine on registers -----------
-      // Positions are tile-local k-mer indices.  In-block prefix minima keep the earliest position
+      // Positions are offsets from the thread's first k-mer o0 (constants in the scans; -1 is the
+      // k-mer before it).  In-block prefix minima keep the earliest position
       // on ties (strict <), suffix minima the earliest too (<=); a window's suffix part lies left of
       // its prefix part, so ties between the two go to the suffix.
       V xn[WM1];  // the next thread's first w-1 keys
@@ -286,32 +289,32 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 #pragma unroll
       for (int b2 = 0; b2 < NB; ++b2) {
         P[b2 * W] = x[b2 * W];
-        Pp[b2 * W] = o0 + b2 * W;
+        Pp[b2 * W] = b2 * W;
 #pragma unroll
         for (int i = 1; i < W; ++i) {
           const int j = b2 * W + i;
           const bool c = x[j] < P[j - 1];
           P[j] = c ? x[j] : P[j - 1];
-          Pp[j] = c ? (uint32_t)(o0 + j) : Pp[j - 1];
+          Pp[j] = c ? (uint32_t)j : Pp[j - 1];
         }
         S[b2 * W + W - 1] = x[b2 * W + W - 1];
-        Sp[b2 * W + W - 1] = o0 + b2 * W + W - 1;
+        Sp[b2 * W + W - 1] = b2 * W + W - 1;
 #pragma unroll
         for (int i = W - 2; i >= 0; --i) {
           const int j = b2 * W + i;
           const bool c = x[j] <= S[j + 1];
           S[j] = c ? x[j] : S[j + 1];
-          Sp[j] = c ? (uint32_t)(o0 + j) : Sp[j + 1];
+          Sp[j] = c ? (uint32_t)j : Sp[j + 1];
         }
       }
       if (W > 1) {
         Pn[0] = xn[0];
-        Pnp[0] = o0 + VPT;
+        Pnp[0] = VPT;
 #pragma unroll
         for (int i = 1; i < W - 1; ++i) {
           const bool c = xn[i] < Pn[i - 1];
           Pn[i] = c ? xn[i] : Pn[i - 1];
-          Pnp[i] = c ? (uint32_t)(o0 + VPT + i) : Pnp[i - 1];
+          Pnp[i] = c ? (uint32_t)(VPT + i) : Pnp[i - 1];
         }
       }
 #pragma unroll
@@ -329,8 +332,8 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
         }
       }
       // pick of the window just before this thread's first: k-mer ifirst-1 and this block's first w-1
-      ypprev = W > 1 ? (xprev <= P[W > 1 ? W - 2 : 0] ? (uint32_t)(o0 - 1) : Pp[W > 1 ? W - 2 : 0])
-                                    : (uint32_t)(o0 - 1);
+      ypprev = W > 1 ? (xprev <= P[W > 1 ? W - 2 : 0] ? 0xFFFFFFFFu : Pp[W > 1 ? W - 2 : 0])
+                                    : 0xFFFFFFFFu;
     } else {
       // ---- chunks of 16 k-mers: window [o, o + w - 1] = suffix of o's chunk, the whole chunks
       // between, and a prefix of the chunk holding o + w - 1 (Eq. 2 with blocks shorter than w).
@@ -481,7 +484,14 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     if (o0 < w) rmask &= ~((1u << (w - o0 < VPT ? w - o0 : VPT)) - 1u);
     if (o0 + VPT > w + TW) rmask &= (1u << (w + TW - o0 > 0 ? w + TW - o0 : 0)) - 1u;
     unsigned emask = 0, firstmask = 0;
-    {
+    if (pvalid && vmask == (1u << VPT) - 1u) {  // every window valid (the common case)
+      uint32_t pp = ypprev;
+#pragma unroll
+      for (int j = 0; j < VPT; ++j) {
+        emask |= (unsigned)(yp[j] != pp) << j;
+        pp = yp[j];
+      }
+    } else {
       bool pv = pvalid;  // validity of the window before (not limited to this tile's range)
       uint32_t pp = ypprev;
 #pragma unroll
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
 #pragma unroll
       for (int j = 0; j < VPT; ++j) {
         if ((emask >> j) & 1u) {
-          uint32_t pos = (uint32_t)(i0 + (long long)yp[j]);
+          uint32_t pos = pos_base + yp[j];
           if (BAR == BAR_READS) {
             const uint32_t rd = g_lo + qj[BAR == BAR_READS ? j : 0];
             pos = (uint32_t)((long long)pos - a.bar[rd]);
