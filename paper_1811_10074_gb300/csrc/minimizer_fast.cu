@@ -27,6 +27,7 @@
 //   wins ties against its prefix part (right).  Every window then knows its pick's position, and a
 //   window stores a pick when its position differs from the previous window's.
 #include <cstdio>
+#include <type_traits>
 
 #include "../../include/sws.h"
 #include "common.cuh"
@@ -227,24 +228,28 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       const uint32_t v0 = __funnelshift_r(sw[q], sw[q + 1], s);  // bases r .. r+15
       const uint32_t v1 = __funnelshift_r(sw[q + 1], sw[q + 2], s);
       const int k = a.k;
-      if (sizeof(V) == 4) {
-        const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+      // one loop per key mode, so the mode test is not repeated for every k-mer
+      auto keys = [&](auto mode_c) {
+        constexpr int MODE = decltype(mode_c)::value;
+        if (sizeof(V) == 4) {
+          const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-          const uint32_t v = key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), a.mode, kmask);
-          x[j] = (V)v;
-        }
-      } else {
-        const uint32_t v2 = __funnelshift_r(sw[q + 2], sw[q + 3], s);
-        const unsigned long long kmask = 2 * k == 64 ? ~0ull : ((1ull << (2 * k)) - 1ull);
+          for (int j = 0; j < VPT; ++j)
+            x[j] = (V)key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), MODE, kmask);
+        } else {
+          const uint32_t v2 = __funnelshift_r(sw[q + 2], sw[q + 3], s);
+          const unsigned long long kmask = 2 * k == 64 ? ~0ull : ((1ull << (2 * k)) - 1ull);
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-          const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
-                                         __funnelshift_r(v0, v1, 2 * j);
-          const unsigned long long v = key_value64(kmer64(w64, k, kmask), a.mode, kmask);
-          x[j] = (V)v;
+          for (int j = 0; j < VPT; ++j) {
+            const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
+                                           __funnelshift_r(v0, v1, 2 * j);
+            x[j] = (V)key_value64(kmer64(w64, k, kmask), MODE, kmask);
+          }
         }
-      }
+      };
+      if (a.mode == SWS_MINI_HASH) keys(std::integral_constant<int, SWS_MINI_HASH>{});
+      else if (a.mode == SWS_MINI_CANONICAL) keys(std::integral_constant<int, SWS_MINI_CANONICAL>{});
+      else keys(std::integral_constant<int, SWS_MINI_FWD>{});
     } else {
       const uint32_t *sk = reinterpret_cast<const uint32_t *>(stage);
       const int r = (int)(i0 - stg.gb0 / 4) + t * VPT;

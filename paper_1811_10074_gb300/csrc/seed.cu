@@ -2,8 +2,9 @@
 // Sec. 2.4 (Fig. 1): for each query seed, the seed pointer table (bucket offsets) and the sorted
 // position table give the run of reference hits with the same seed hash.
 //
-//   k_seed_lookup  one thread per query: bucket range from the pointer table, then two binary
-//                  searches in the bucket for the run of equal hashes -> (first, count).
+//   k_seed_lookup  one thread per query: bucket range from the pointer table, a binary search in
+//                  the bucket for the first equal hash, and a galloping search for the end of
+//                  the run of equal hashes -> (first, count).
 //   k_hits_count   per tile of queries, the number of hits kept by the repeat filter (a seed with
 //                  more than max_occ hits is dropped);
 //   k_hits_scan    exclusive scan of the tile totals (one CTA, 64-bit);
@@ -44,20 +45,33 @@ __global__ void __launch_bounds__(QNT) k_seed_lookup(const void *__restrict__ so
     return;
   }
   uint64_t lo = offsets[b], hi = offsets[b + 1];
+  const uint64_t end = hi;
   while (lo < hi) {  // first index of the bucket with hash >= q
     const uint64_t mid = lo + (hi - lo) / 2;
     if (hash_at<WIDE>(sorted_hash, mid) < q) lo = mid + 1;
     else hi = mid;
   }
   const uint64_t a = lo;
-  hi = offsets[b + 1];
-  while (lo < hi) {  // first index with hash > q
-    const uint64_t mid = lo + (hi - lo) / 2;
-    if (hash_at<WIDE>(sorted_hash, mid) <= q) lo = mid + 1;
-    else hi = mid;
+  uint64_t c = 0;
+  if (a < end && hash_at<WIDE>(sorted_hash, a) == q) {
+    // the end of the run by galloping from its start: a seed usually has one or a few hits, so the
+    // first probe (next to a, in the same cache line) mostly settles it
+    uint64_t known = a + 1, step = 1, probe = a + 1;  // [a, known) all hold q
+    while (probe < end && hash_at<WIDE>(sorted_hash, probe) == q) {
+      known = probe + 1;
+      step <<= 1;
+      probe = a + step;
+    }
+    uint64_t top = probe < end ? probe : end;  // hash at top differs from q, or top = end
+    while (known < top) {
+      const uint64_t mid = known + (top - known) / 2;
+      if (hash_at<WIDE>(sorted_hash, mid) == q) known = mid + 1;
+      else top = mid;
+    }
+    c = known - a;
   }
   first[i] = a;
-  count[i] = (uint32_t)(lo - a);
+  count[i] = (uint32_t)c;
 }
 
 __device__ __forceinline__ uint32_t kept(uint32_t c, uint32_t max_occ) { return (max_occ == 0 || c <= max_occ) ? c : 0u; }
