@@ -470,12 +470,30 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       };
       pvalid = valid_at(pf, q);
       vmask = 0;
+      if (q == nb || bar_end(q) > ifirst + VPT - 1) {
+        // No barrier ends among this thread's windows (the common case, also in read batches), so
+        // barrier q bounds them all: the valid ones are p in [0, nwin) with p + span - 1 below its
+        // start, a run of consecutive j.
+        long long jlo = -ifirst, jhi = (long long)nwin - ifirst;
+        if (q < nb) {
+          const long long lim = bar_start(q) - span + 1 - ifirst;
+          if (lim < jhi) jhi = lim;
+        }
+        if (jlo < 0) jlo = 0;
+        if (jhi > VPT) jhi = VPT;
+        if (jhi > jlo) vmask = ((1u << jhi) - 1u) & ~((1u << jlo) - 1u);
+        if (BAR == BAR_READS) {
 #pragma unroll
-      for (int j = 0; j < VPT; ++j) {
-        const long long p = ifirst + j;
-        while (q < nb && bar_end(q) <= p) ++q;
-        if (BAR == BAR_READS) qj[BAR == BAR_READS ? j : 0] = q;
-        vmask |= (unsigned)valid_at(p, q) << j;
+          for (int j = 0; j < (BAR == BAR_READS ? VPT : 1); ++j) qj[j] = q;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+          const long long p = ifirst + j;
+          while (q < nb && bar_end(q) <= p) ++q;
+          if (BAR == BAR_READS) qj[BAR == BAR_READS ? j : 0] = q;
+          vmask |= (unsigned)valid_at(p, q) << j;
+        }
       }
     }
     if (!ok) {
