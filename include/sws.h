@@ -186,8 +186,9 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
  * graph (one persistent minimizer launch plus its scan, gather and fix-up kernels) whatever the
  * size of the batch, reading the sizes from a device descriptor.  Results are those of
  * sws_minimizers_batch on the same reads.
- *   options: SWS_BATCH_DEFAULT picks the kernel specialized on w when it applies (4 <= w <= 16,
- *            k <= 16), SWS_BATCH_TUNE times it against the single-kernel look-back path on a
+ *   options: SWS_BATCH_DEFAULT takes the staged path (the staged kernel for 4 <= w <= 256 and
+ *            k <= 32, otherwise the generic kernel writing per-tile slots, then a scan and a
+ *            gather), SWS_BATCH_TUNE times it against the single-kernel look-back path on a
  *            synthetic batch of the largest size and keeps the faster (see sws_batch_io.tuned_ms),
  *            SWS_BATCH_LOOKBACK forces the look-back path.
  * One run may be in flight per object: sws_batch_run waits for the previous run to finish before
