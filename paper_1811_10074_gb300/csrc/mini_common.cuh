@@ -110,6 +110,21 @@ __device__ __forceinline__ unsigned long long wang_mix64(unsigned long long x, u
   x = (x * 0x80000001ull) & m;
   return x;
 }
+// The same mix for a mask m = 2^b - 1 with 32 < b <= 64, given as its high word: the low word
+// of m is all ones, so only the high word is ever masked.
+__device__ __forceinline__ unsigned long long wang_mix64_wide(unsigned long long x, uint32_t mhi) {
+  auto mask = [mhi](unsigned long long v) {
+    return ((unsigned long long)((uint32_t)(v >> 32) & mhi) << 32) | (uint32_t)v;
+  };
+  x = mask(x * 0x1FFFFFull + 0xFFFFFFFFFFFFFFFFull);
+  x ^= x >> 24;
+  x = mask(x * 265ull);
+  x ^= x >> 14;
+  x = mask(x * 21ull);
+  x ^= x >> 28;
+  x = mask(x * 0x80000001ull);
+  return x;
+}
 // Reverse the order of the 2-bit groups of a word.
 __device__ __forceinline__ uint32_t rev_pairs32(uint32_t x) {
   x = __brev(x);
@@ -148,6 +163,12 @@ __device__ __forceinline__ unsigned long long key_value64(const Kmer64 &q, int m
   if (mode == SWS_MINI_FWD) return q.fwd;
   const unsigned long long c = q.fwd < q.rc ? q.fwd : q.rc;
   return mode == SWS_MINI_CANONICAL ? c : wang_mix64(c, kmask);
+}
+// key_value64 for k > 16 (2k > 32 bits), the mask given by its high word.
+__device__ __forceinline__ unsigned long long key_value64_wide(const Kmer64 &q, int mode, uint32_t kmask_hi) {
+  if (mode == SWS_MINI_FWD) return q.fwd;
+  const unsigned long long c = q.fwd < q.rc ? q.fwd : q.rc;
+  return mode == SWS_MINI_CANONICAL ? c : wang_mix64_wide(c, kmask_hi);
 }
 
 // ---- keys -----------------------------------------------------------------------------------

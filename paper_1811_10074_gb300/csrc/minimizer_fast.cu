@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
           for (int j = 0; j < VPT; ++j) {
             const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
                                            __funnelshift_r(v0, v1, 2 * j);
-            x[j] = (V)key_value64(kmer64(w64, k, kmask), MODE, kmask);
+            x[j] = (V)key_value64_wide(kmer64(w64, k, kmask), MODE, (uint32_t)(kmask >> 32));  // 2k > 32 here
           }
         }
       };
