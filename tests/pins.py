@@ -112,6 +112,92 @@ def alg2_vector_input(op, xs, w, P):
     return out
 
 
+def short_block_window_sums(op, xs, w, B):
+    """Eq. 2 combined over blocks of B < w inputs (the reading behind the chunked minimizer kernel):
+    window p = suffix of its first block from p, the totals of the whole blocks inside it, and the
+    prefix of its last block up to p + w - 1, combined left to right."""
+    f, _ = PY_OPS[op]
+    assert B < w
+    out = []
+    for p in range(len(xs) - w + 1):
+        q = p + w - 1
+        bp, bq = p // B, q // B
+        acc = xs[p]
+        for t in range(p + 1, (bp + 1) * B):     # suffix of the first block
+            acc = f(acc, xs[t])
+        for b in range(bp + 1, bq):              # whole blocks
+            tot = xs[b * B]
+            for t in range(b * B + 1, (b + 1) * B):
+                tot = f(tot, xs[t])
+            acc = f(acc, tot)
+        pre = xs[bq * B]                          # prefix of the last block
+        for t in range(bq * B + 1, q + 1):
+            pre = f(pre, xs[t])
+        out.append(f(acc, pre))
+    return out
+
+
+def short_block_argmin(xs, w, B):
+    """The same decomposition for the minimum with the position of its leftmost occurrence, with
+    the chunked kernel's tie rules: prefix minima and the left-to-right combination take a later
+    element only when strictly smaller, suffix minima keep the earlier one on ties."""
+    out = []
+    for p in range(len(xs) - w + 1):
+        q = p + w - 1
+        bp, bq = p // B, q // B
+        sv, sp = xs[(bp + 1) * B - 1], (bp + 1) * B - 1
+        for t in range((bp + 1) * B - 2, p - 1, -1):  # suffix scan, backwards, <= keeps the earlier
+            if xs[t] <= sv:
+                sv, sp = xs[t], t
+        acc = (sv, sp)
+        for b in range(bp + 1, bq):
+            tv, tp = xs[b * B], b * B
+            for t in range(b * B + 1, (b + 1) * B):
+                if xs[t] < tv:
+                    tv, tp = xs[t], t
+            if tv < acc[0]:
+                acc = (tv, tp)
+        pv, pp = xs[bq * B], bq * B
+        for t in range(bq * B + 1, q + 1):
+            if xs[t] < pv:
+                pv, pp = xs[t], t
+        if pv < acc[0]:
+            acc = (pv, pp)
+        out.append(acc)
+    return out
+
+
+def check_eq2_short_blocks(lib, seed=3, nmax=40):
+    """Eq. 2 (oracle) = the combination over blocks shorter than w, every operator (the affine
+    maps are not commutative, so the order of the pieces matters), every B < w <= n; and for the
+    minimum, the leftmost argmin of every window by brute force (few distinct values: many ties)."""
+    rng = np.random.default_rng(seed)
+    for op in PY_OPS:
+        for n in (17, 23, nmax):
+            xs = _rand_elems(op, n, rng)
+            for w in range(2, n + 1):
+                got = _from_oracle_output(op, O.sliding_sum(op, w, _to_oracle_input(op, xs), lib=lib))
+                for B in (1, 2, 3, 5, 16):
+                    if B >= w:
+                        continue
+                    ref = short_block_window_sums(op, xs, w, B)
+                    if op == "add_f32":
+                        for p, (a, b) in enumerate(zip(got, ref)):
+                            assert _close_f(a, b, sum(abs(v) for v in xs[p:p + w])), (op, n, w, B, p)
+                    else:
+                        assert got == ref, (op, n, w, B)
+    for trial in range(40):
+        n = int(rng.integers(17, 90))
+        xs = [int(v) for v in rng.integers(0, 4, size=n)]
+        for w in (17, 18, 31, 32, 33, 50, 64, 65):
+            if w > n:
+                continue
+            got = short_block_argmin(xs, w, 16)
+            for p, (v, pos) in enumerate(got):
+                seg = xs[p:p + w]
+                assert v == min(seg) and pos == p + seg.index(min(seg)), (n, w, p)
+
+
 def _rand_elems(op, n, rng):
     if op == "affine_u32":
         return [(int(a), int(b)) for a, b in rng.integers(0, 1 << 32, size=(n, 2), dtype=np.uint64)]
@@ -584,6 +670,7 @@ def check_strands(lib):
 
 ALL_CHECKS = [
     check_eq2_vs_algorithms,
+    check_eq2_short_blocks,
     check_eq2_closed_forms,
     check_prefix_difference,
     check_sampled_matches_full,
