@@ -197,6 +197,27 @@ def make_inputs(n: int, device, seed: int):
     return {"add_i32": x32, "min_i32": x32, "max_i32": x32, "xor_i32": x32, "affine_u32": xa, "add_f32": xf}
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # lscpu missing: fall through
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(n_sample: int, seed: int = 42):
     """The oracle (plain O(wN) Eq. 2, single thread) on n_sample elements per case."""
     import oracle
@@ -313,7 +334,8 @@ def run_ours(args, world, rank, local):
         v, dt = cpu_baseline(args.cpu_sample)
         result["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                                   "sample": f"{args.cpu_sample} elements per (op, w) case, all {len(OPS) * len(WS)} cases, "
-                                            f"{dt:.1f} s single-threaded naive O(wN)"}
+                                            f"{dt:.1f} s single-threaded naive O(wN)",
+                                  "cpu_model": host_cpu_model(), "host_cores": os.cpu_count()}
     if not args.no_extras and rank == 0:
         result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
         result["genome_table"] = genome_table_extras(dev, ctx, args.genome_n)
@@ -441,17 +463,22 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
                                         "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
     del seq
     torch.cuda.empty_cache()
-    # paper-equivalent: sliding minimum over 2^28 precomputed 30-bit hashes, w = 10
+    # paper-equivalent: sliding minimum over 2^28 precomputed 30-bit hashes, w = 10, and the sweep
+    # w = 4..17 (the window lengths of the paper's timing figure)
     m = 1 << 28
     keys = synth.uint32_hashes(m, device=dev)
-    cap = m // 4
-    ms = time_call(lambda: P.minimizers_from_keys(keys, 10, capacity=cap, ctx=ctx, stream=stream, sync=False), 5,
-                   stream)
-    _, _, cnt = P.minimizers_from_keys(keys, 10, capacity=cap, ctx=ctx, stream=stream, sync=False)
-    picks = int(cnt.item())
-    b = 4 * m + 8 * picks
-    out["sliding_min_keys_2^28_w10"] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
-                                        "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    sweep = {}
+    for w in range(4, 18):
+        cap = int(m * 2.6 / (w + 1)) + 1024
+        ms = time_call(lambda: P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False), 5,
+                       stream)
+        _, _, cnt = P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
+        picks = int(cnt.item())
+        b = 4 * m + 8 * picks
+        sweep[w] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
+                    "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    out["sliding_min_keys_2^28_w10"] = sweep[10]
+    out["sliding_min_keys_2^28_w4_17"] = {str(w): {"ms": v["ms"], "gbs": v["gbs"]} for w, v in sweep.items()}
     return out
 
 
@@ -688,7 +715,8 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32,u32x2,f32", "data": "synthetic (SplitMix64 seed 42)",
         "config": {"workload": WORKLOAD, "n": ns, "sample": f"{ns} elements per case (bounded sample of 2^28)"},
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{ns} elements per (op, w) case, all 30 cases per step"},
+                         "sample": f"{ns} elements per (op, w) case, all 30 cases per step",
+                         "cpu_model": host_cpu_model(), "host_cores": os.cpu_count()},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
