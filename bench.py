@@ -337,7 +337,7 @@ def run_ours(args, world, rank, local):
                                             f"{dt:.1f} s single-threaded naive O(wN)",
                                   "cpu_model": host_cpu_model(), "host_cores": os.cpu_count()}
     if not args.no_extras and rank == 0:
-        result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n)
+        result["minimizers"] = minimizer_extras(dev, ctx, args.mini_n, with_cpu=not args.no_cpu)
         result["genome_table"] = genome_table_extras(dev, ctx, args.genome_n)
         result["batched_reads"] = batch_extras(dev, ctx)
         result["serving"] = serve_extras(ctx)
@@ -433,7 +433,7 @@ def time_call(fn, reps: int, stream):
     return a.elapsed_time(b) / reps
 
 
-def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
+def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     """Secondary numbers: fused minimizers (Gbp/s) and the paper-equivalent sliding minimum over
     precomputed hashes (GB/s vs HBM)."""
     import paper_1811_10074_gb300 as P
@@ -463,10 +463,13 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
                                         "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
     del seq
     torch.cuda.empty_cache()
-    # paper-equivalent: sliding minimum over 2^28 precomputed 30-bit hashes, w = 10, and the sweep
-    # w = 4..17 (the window lengths of the paper's timing figure)
+    # paper-equivalent (Sec. 4): sliding minimum over the hashed canonical 15-mers of a uniform
+    # genome, 2^28 of them (sws_kmers with the hash), w = 10 and the sweep w = 4..17 (the window
+    # lengths of the paper's timing figure)
     m = 1 << 28
-    keys = synth.uint32_hashes(m, device=dev)
+    gseq = synth.acgt_uniform_packed(m + 14, seed=44, device=dev)
+    keys = P.kmers(gseq, m + 14, 15, "hash", ctx=ctx, stream=stream)
+    del gseq
     sweep = {}
     for w in range(4, 18):
         cap = int(m * 2.6 / (w + 1)) + 1024
@@ -478,8 +481,51 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31):
         sweep[w] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
                     "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
     out["sliding_min_keys_2^28_w10"] = sweep[10]
-    out["sliding_min_keys_2^28_w4_17"] = {str(w): {"ms": v["ms"], "gbs": v["gbs"]} for w, v in sweep.items()}
+    out["sliding_min_keys_2^28_w4_17"] = {str(w): {"ms": v["ms"], "gbs": v["gbs"], "frac_hbm": v["frac_hbm"]}
+                                          for w, v in sweep.items()}
+    out["keys_input"] = "2^28 hashed canonical 15-mers (sws_kmers, hash) of a uniform ACGT sequence, seed 44"
+    if with_cpu:
+        out["cpu_baseline"] = minimizer_cpu_baseline(keys, m, sweep)
     return out
+
+
+def minimizer_cpu_baseline(keys, m, sweep, sample_keys: int = 1 << 24, sample_bases: int = 1 << 22):
+    """The oracle on the host cores, on bounded samples of the same inputs: the sliding minimum
+    over the first `sample_keys` hashed 15-mers for w = 4..17 as the naive per-window scan (the
+    paper's "Array"), the queue-based scan ("Dequeue"), each on one core, and the naive scan
+    chunked over all cores; fused minimizers (k = 15, w = 10) of `sample_bases` uniform bases on
+    one core and chunked over all cores.  Units as the GPU figures (GB/s of 4 B per key in + 8 B
+    per pick out; Gbp/s)."""
+    import oracle
+    from paper_1811_10074_gb300 import synth
+    cores = os.cpu_count() or 1
+    ks = keys[:sample_keys].cpu().numpy().view(np.uint32).astype(np.uint64)
+    res = {"cpu_model": host_cpu_model(), "host_cores": cores, "kind": "oracle",
+           "sample": f"first {sample_keys} of the GPU's 2^28 keys per w; {sample_bases} uniform bases (seed 45) "
+                     f"for the fused k=15 w=10 row", "keys": {}}
+    for w in range(4, 18):
+        row = {}
+        for name, fn, cs in (("array_1core", lambda: oracle.minimizers_from_keys(ks, w), 1),
+                             ("dequeue_1core", lambda: oracle.minimizers_from_keys(ks, w, deque=True), 1),
+                             (f"array_{cores}cores", lambda: oracle.minimizers_from_keys_chunked(ks, w, cores), cores)):
+            t0 = time.perf_counter()
+            h, _ = fn()
+            dt = time.perf_counter() - t0
+            row[name] = {"s": round(dt, 3), "gbs": round((4 * ks.size + 8 * h.size) / dt / 1e9, 4), "cores": cs}
+        row["gpu_vs_best_cpu"] = round(sweep[w]["gbs"] / max(v["gbs"] for v in row.values()), 1)
+        res["keys"][str(w)] = row
+    seq = synth.acgt_uniform_packed(sample_bases, seed=45)
+    fused = {}
+    for name, fn, cs in (("naive_1core", lambda: oracle.minimizers(seq, sample_bases, 15, 10), 1),
+                         ("dequeue_1core", lambda: oracle.minimizers(seq, sample_bases, 15, 10, deque=True), 1),
+                         (f"naive_{cores}cores", lambda: oracle.minimizers_chunked(seq, sample_bases, 15, 10, cores),
+                          cores)):
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        fused[name] = {"s": round(dt, 3), "gbp_s": round(sample_bases / dt / 1e9, 4), "cores": cs}
+    res["fused_k15_w10"] = fused
+    return res
 
 
 def genome_table_extras(dev, ctx, n: int = 3_100_000_000, reps: int = 3, bucket_bits: int = 24):
@@ -737,7 +783,7 @@ def main():
         ctx = P.default_context(dev.index)
         if rank == 0:
             if args.section == "minimizers":
-                print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n)}), flush=True)
+                print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n, with_cpu=not args.no_cpu)}), flush=True)
             elif args.section == "table":
                 print(json.dumps({"genome_table": genome_table_extras(dev, ctx, args.genome_n)}), flush=True)
             elif args.section == "batch":

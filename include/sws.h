@@ -102,6 +102,17 @@ sws_status sws_sync(sws_ctx *ctx, void *stream);
  * context stays usable.  Nothing faults, traps or hangs.  which outside {0, 1}: SWS_ERR_INVALID. */
 sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream);
 
+/* Failure self-test of the ordered minimizer output (no counterpart in the paper).  Runs the
+ * single-kernel (look-back) minimizer path -- the path sws_minimizers takes for small inputs and
+ * sws_minimizers_noalloc always takes -- with k = 15, w = 10 over three tiles of a zeroed scratch
+ * sequence in the context's workspace, its staging copies announced on the tiles' mbarriers but
+ * never issued, so every tile's bounded copy wait runs out.  count_out (device uint64) is set to
+ * all ones when the call is queued and must stay all ones: a tile whose input never arrived
+ * publishes a failure in place of its count, every later tile then fails in turn, and no tile
+ * writes the total.  The next sws_sync returns SWS_ERR_TIMEOUT and the context stays usable.
+ * Takes about a second on the device; nothing faults, traps or hangs. */
+sws_status sws_selftest_minimizer_timeout(sws_ctx *ctx, uint64_t *count_out, void *stream);
+
 #define SWS_VARIANT_COUNT 6
 
 /* Autotuner for the sliding sum: on a scratch input of n elements (a fixed pseudo-random pattern
@@ -159,6 +170,32 @@ sws_status sws_kmers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int ki
 sws_status sws_minimizers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
                           const int64_t *nblocks, uint64_t n_nblocks, void *hash_out, uint32_t *pos_out,
                           uint64_t capacity, uint64_t *count_out, void *stream);
+
+/* Capacity query for sws_minimizers (Sec. 2.4): the exact number of picks sws_minimizers would
+ * store for the same arguments, written to count_out (device uint64), without writing any pick.
+ * The same kernels run in a counting mode (no staging area), so the count is exact; a capacity of
+ * *count_out then suffices for sws_minimizers.  Errors and limits as for sws_minimizers.  Uses
+ * workspace (about 12 bytes per 4000 windows). */
+sws_status sws_minimizers_count(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                                const int64_t *nblocks, uint64_t n_nblocks, uint64_t *count_out, void *stream);
+
+/* The seed table of a packed sequence in one call (Sec. 2.4, Fig. 1): its minimizers (as
+ * sws_minimizers with the same k, w, mode and N-blocks), then the position table and pointer
+ * table built from the (key, position) hits as sws_kmer_table does with hash_bits = 2k.
+ *   sorted_hash/sorted_pos : device outputs of `capacity` entries (sorted_hash uint32 when
+ *                            2k <= 32, else uint64): the hits sorted by key, positions ascending
+ *                            within a key.  They also hold the unsorted hits while the table is
+ *                            built, so no second hit array is allocated.
+ *   bucket_offsets         : device uint64 [2^bucket_bits + 1], 0 <= bucket_bits <= min(2k, 32).
+ *   count                  : HOST uint64 receiving the number of hits m.
+ * The call waits for the minimizers to finish (the sort is sized by m) and then queues the sort on
+ * `stream`; it returns with the sort still running.  m > capacity: *count = m, SWS_ERR_CAPACITY,
+ * outputs undefined.  A bounded device-side wait that ran out while finding the minimizers:
+ * SWS_ERR_TIMEOUT.  Uses workspace (about 16 bytes per hit, 24 when 2k > 32). */
+sws_status sws_build_table(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                           const int64_t *nblocks, uint64_t n_nblocks, int bucket_bits, void *sorted_hash,
+                           uint32_t *sorted_pos, uint64_t capacity, uint64_t *bucket_offsets, uint64_t *count,
+                           void *stream);
 
 /* Paper-equivalent task of Sec. 4: deduplicated sliding minimum, with (value, position) keys,
  * over a precomputed array of m uint32 key values (e.g. hashed 15-mers).  Outputs as for

@@ -74,6 +74,8 @@ def load(path: str | None = None):
         lib.oracle_minimizers_batch.argtypes = [vp, vp, u64, i32, i32, i32, vp, vp, u64, vp]
         lib.oracle_minimizers_from_keys.restype = u64
         lib.oracle_minimizers_from_keys.argtypes = [vp, u64, i32, vp, vp, u64]
+        lib.oracle_minimizers_from_keys_deque.restype = u64
+        lib.oracle_minimizers_from_keys_deque.argtypes = [vp, u64, i32, vp, vp, u64]
         lib.oracle_kmer_table.restype = i32
         lib.oracle_kmer_table.argtypes = [vp, vp, u64, i32, i32, vp, vp, vp]
         lib.oracle_strands.restype = None
@@ -199,17 +201,96 @@ def minimizers_batch(seq, offs, k: int, w: int, mode: str = "hash", lib=None):
     return h[:cnt], p[:cnt], po
 
 
-def minimizers_from_keys(keys, w: int, lib=None):
-    """Deduplicated (key, position) sliding minima over a precomputed key array."""
+def minimizers_from_keys(keys, w: int, deque: bool = False, lib=None):
+    """Deduplicated (key, position) sliding minima over a precomputed key array (naive per-window
+    scan, or with ``deque`` the queue-based scan)."""
     lib = lib or load()
     kv = _np(keys)
-    kv = np.ascontiguousarray(kv.astype(np.uint64) if kv.dtype != np.uint64 else kv)
+    if kv.dtype != np.uint64:
+        kv = kv.view(np.uint32) if kv.dtype == np.int32 else kv
+        kv = kv.astype(np.uint64)
+    kv = np.ascontiguousarray(kv)
     m = kv.size
     cap = max(m - w + 1, 1)
     h = np.zeros(cap, dtype=np.uint64)
     p = np.zeros(cap, dtype=np.uint32)
-    cnt = int(lib.oracle_minimizers_from_keys(_ptr(kv), m, w, _ptr(h), _ptr(p), cap))
+    fn = lib.oracle_minimizers_from_keys_deque if deque else lib.oracle_minimizers_from_keys
+    cnt = int(fn(_ptr(kv), m, w, _ptr(h), _ptr(p), cap))
     return h[:cnt], p[:cnt]
+
+
+# ------------------------------------------------------------------------------------------
+# Chunked multi-threaded drivers (for timing the oracle on all host cores).  They split the
+# windows into contiguous ranges, run the plain oracle above on each range's inputs (the range
+# plus the w - 1 (+ k - 1) elements its last windows reach) in a thread each -- ctypes releases
+# the GIL during the C call -- and join the per-range picks in order.  A range's first window
+# always stores its pick, so where that pick is the previous range's last pick (the same
+# position: positions strictly increase) it is dropped once.  The arithmetic is the oracle's.
+# ------------------------------------------------------------------------------------------
+
+def _join_ranges(parts):
+    hs, ps = [], []
+    last = None
+    for h, p in parts:
+        if last is not None and p.size and int(p[0]) == last:
+            h, p = h[1:], p[1:]
+        if p.size:
+            last = int(p[-1])
+        hs.append(h)
+        ps.append(p)
+    if not hs:
+        return np.zeros(0, np.uint64), np.zeros(0, np.uint32)
+    return np.concatenate(hs), np.concatenate(ps)
+
+
+def minimizers_from_keys_chunked(keys, w: int, threads: int, deque: bool = False, lib=None):
+    """:func:`minimizers_from_keys` with the windows split over ``threads`` threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib = lib or load()
+    kv = _np(keys)
+    if kv.dtype != np.uint64:
+        kv = kv.view(np.uint32) if kv.dtype == np.int32 else kv
+        kv = kv.astype(np.uint64)
+    kv = np.ascontiguousarray(kv)
+    m = kv.size
+    nwin = max(m - w + 1, 0)
+    threads = max(1, min(int(threads), max(nwin, 1)))
+    bounds = [nwin * t // threads for t in range(threads + 1)]
+
+    def one(t):
+        p0, p1 = bounds[t], bounds[t + 1]
+        if p1 <= p0:
+            return np.zeros(0, np.uint64), np.zeros(0, np.uint32)
+        h, p = minimizers_from_keys(kv[p0:p1 + w - 1], w, deque=deque, lib=lib)
+        return h, (p.astype(np.uint64) + p0).astype(np.uint32)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, range(threads)))
+    return _join_ranges(parts)
+
+
+def minimizers_chunked(seq, n: int, k: int, w: int, threads: int, mode: str = "hash", deque: bool = False,
+                       lib=None):
+    """:func:`minimizers` of a packed sequence without N-blocks, the windows split over ``threads``
+    threads (ranges start at multiples of 4 bases, i.e. at byte boundaries of the packing)."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib = lib or load()
+    s = _np(seq, np.uint8)
+    nwin = max(n - (w + k - 1) + 1, 0)
+    threads = max(1, min(int(threads), max(nwin // 4, 1)))
+    bounds = [(nwin * t // threads) // 4 * 4 for t in range(threads)] + [nwin]
+
+    def one(t):
+        p0, p1 = bounds[t], bounds[t + 1]
+        if p1 <= p0:
+            return np.zeros(0, np.uint64), np.zeros(0, np.uint32)
+        nb = p1 - p0 + w + k - 2  # bases the range's windows cover
+        h, p = minimizers(s[p0 // 4:(p0 + nb + 3) // 4], nb, k, w, mode=mode, deque=deque, lib=lib)
+        return h, (p.astype(np.uint64) + p0).astype(np.uint32)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, range(threads)))
+    return _join_ranges(parts)
 
 
 def kmer_table(hashes, pos, hash_bits: int, bucket_bits: int, lib=None):

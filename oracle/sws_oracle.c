@@ -386,6 +386,38 @@ uint64_t oracle_minimizers_from_keys(const uint64_t *key, uint64_t m, int w, uin
     return o.count;
 }
 
+/* The same task with the queue-based O(N) sliding minimum the paper times as "Dequeue" (Sec. 4,
+ * after the method it cites in Sec. 2.4): a deque of key indices whose keys never decrease from
+ * front to back; the front is the window's leftmost least key. */
+uint64_t oracle_minimizers_from_keys_deque(const uint64_t *key, uint64_t m, int w, uint64_t *hash_out,
+                                           uint32_t *pos_out, uint64_t cap)
+{
+    sink_t o;
+    uint64_t i, front = 0, back = 0, prev = 0;
+    uint64_t *q;
+    int have_prev = 0;
+    o.hash_out = hash_out;
+    o.pos_out = pos_out;
+    o.cap = cap;
+    o.count = 0;
+    if (w < 1 || m < (uint64_t)w) return 0;
+    q = (uint64_t *)malloc((size_t)m * sizeof(uint64_t));
+    for (i = 0; i < m; ++i) {
+        /* drop queued candidates that the new key beats; an equal key keeps the older one */
+        while (back > front && key[q[back - 1]] > key[i]) back--;
+        q[back++] = i;
+        if (i + 1 >= (uint64_t)w) {
+            const uint64_t start = i + 1 - (uint64_t)w; /* window [start, i] */
+            while (q[front] < start) front++;           /* candidates that left the window */
+            if (!have_prev || q[front] != prev) sink_put(&o, key[q[front]], q[front]);
+            prev = q[front];
+            have_prev = 1;
+        }
+    }
+    free(q);
+    return o.count;
+}
+
 /* ------------------------------------------------------------------------------------------
  * Seed table (Sec. 2.4): a position table of (seed, position) hits sorted by seed, and a
  * pointer table giving, for every bucket of seed values, where its hits begin.  Bucket of a

@@ -5,6 +5,6 @@ thin ctypes binding and ``synth`` the seeded input generators.  Importing the pa
 load the library; the first call does, and raises if it has not been built.
 """
 
-from .binding import (Batch, Context, Server, SwsError, default_context, kmer_table, kmers,  # noqa: F401
-                      minimizer_strands, minimizers, minimizers_batch, minimizers_from_keys, seed_hits,
-                      seed_lookup, sliding_sum, tune_sliding_sum)
+from .binding import (Batch, Context, Server, SwsError, build_table, default_context, kmer_table,  # noqa: F401
+                      kmers, minimizer_strands, minimizers, minimizers_batch, minimizers_count,
+                      minimizers_from_keys, seed_hits, seed_lookup, sliding_sum, tune_sliding_sum)

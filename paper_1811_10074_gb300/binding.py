@@ -49,12 +49,15 @@ SIGNATURES = {
     "sws_sliding_sum": (i32, [vp, i32, i32, vp, vp, u64, i32, vp]),
     "sws_tune_sliding_sum": (i32, [vp, i32, i32, u64, vp, vp, vp]),
     "sws_selftest_wait_timeout": (i32, [vp, i32, vp]),
+    "sws_selftest_minimizer_timeout": (i32, [vp, vp, vp]),
     "sws_minimizer_strands": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, u64, vp, vp]),
     "sws_seed_lookup": (i32, [vp, vp, u64, i32, i32, vp, vp, u64, vp, vp, vp]),
     "sws_seed_hits": (i32, [vp, vp, vp, u64, ctypes.c_uint32, vp, vp, vp, u64, vp, vp]),
     "sws_kmers": (i32, [vp, vp, u64, i32, i32, vp, vp]),
     "sws_minimizers": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
     "sws_minimizers_from_keys": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp]),
+    "sws_minimizers_count": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, vp, vp]),
+    "sws_build_table": (i32, [vp, vp, u64, i32, i32, i32, vp, u64, i32, vp, vp, u64, vp, ctypes.POINTER(u64), vp]),
     "sws_minimizers_batch": (i32, [vp, vp, vp, u64, u64, i32, i32, i32, vp, vp, u64, vp, vp, vp]),
     "sws_kmer_table": (i32, [vp, vp, vp, u64, i32, i32, vp, vp, vp, vp]),
     "sws_minimizers_noalloc": (i32, [vp, u64, i32, i32, i32, vp, u64, vp, vp, u64, vp, vp]),
@@ -218,6 +221,15 @@ def selftest_wait_timeout(which: str = "lookback", ctx: Context | None = None, s
     _check(load().sws_selftest_wait_timeout(ctx.handle, {"lookback": 0, "mbarrier": 1}[which], _stream(stream)))
 
 
+def selftest_minimizer_timeout(ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """Queue the look-back minimizer kernel with its input copies withheld; returns the device
+    count word (it must stay all ones) -- the next ``Context.sync`` raises SwsError(TIMEOUT)."""
+    ctx = ctx or default_context(torch.cuda.current_device())
+    cnt = torch.zeros(1, dtype=torch.int64, device=torch.device("cuda", ctx.device))
+    _check(load().sws_selftest_minimizer_timeout(ctx.handle, _ptr(cnt), _stream(stream)))
+    return cnt
+
+
 def kmers(seq: torch.Tensor, n: int, k: int, kind: str = "hash", out: torch.Tensor | None = None,
           ctx: Context | None = None, stream=None) -> torch.Tensor:
     """k-mer values (int32 bit patterns when 2k <= 32, else int64)."""
@@ -263,6 +275,51 @@ def minimizers(seq: torch.Tensor, n: int, k: int, w: int, mode: str = "hash", nb
         return h, p, cnt
     h, p, _ = _trim(h, p, cnt, capacity, ctx, stream)
     return h, p
+
+
+def minimizers_count(seq: torch.Tensor, n: int, k: int, w: int, mode: str = "hash",
+                     nblocks: torch.Tensor | None = None, ctx: Context | None = None, stream=None,
+                     sync: bool = True):
+    """Exact number of picks :func:`minimizers` would return (an int; with ``sync=False`` the
+    device count tensor)."""
+    _dev(seq, "seq")
+    ctx = ctx or default_context(seq.device.index)
+    cnt = torch.empty(1, dtype=torch.int64, device=seq.device)
+    nb = 0
+    if nblocks is not None:
+        _dev(nblocks, "nblocks")
+        nb = nblocks.shape[0]
+    _check(load().sws_minimizers_count(ctx.handle, _ptr(seq), int(n), int(k), int(w), MINI_MODES[mode],
+                                       _ptr(nblocks) if nb else vp(0), nb, _ptr(cnt), _stream(stream)))
+    if not sync:
+        return cnt
+    ctx.sync(stream)
+    return int(cnt.item())
+
+
+def build_table(seq: torch.Tensor, n: int, k: int, w: int, bucket_bits: int, mode: str = "hash",
+                nblocks: torch.Tensor | None = None, capacity: int | None = None, ctx: Context | None = None,
+                stream=None):
+    """Minimizers, then the seed table, in one call: (sorted keys, sorted positions, bucket offsets
+    [2^bucket_bits + 1]).  Without a capacity, :func:`minimizers_count` sizes the outputs."""
+    _dev(seq, "seq")
+    ctx = ctx or default_context(seq.device.index)
+    if capacity is None:
+        capacity = minimizers_count(seq, n, k, w, mode, nblocks, ctx=ctx, stream=stream)
+    dev = seq.device
+    sh = torch.empty(max(capacity, 1), dtype=torch.int32 if 2 * k <= 32 else torch.int64, device=dev)
+    sp = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    off = torch.empty((1 << bucket_bits) + 1, dtype=torch.int64, device=dev)
+    nb = 0
+    if nblocks is not None:
+        _dev(nblocks, "nblocks")
+        nb = nblocks.shape[0]
+    m = u64()
+    _check(load().sws_build_table(ctx.handle, _ptr(seq), int(n), int(k), int(w), MINI_MODES[mode],
+                                  _ptr(nblocks) if nb else vp(0), nb, int(bucket_bits), _ptr(sh), _ptr(sp), capacity,
+                                  _ptr(off), ctypes.byref(m), _stream(stream)))
+    c = int(m.value)
+    return sh[:c], sp[:c], off
 
 
 def minimizers_from_keys(keys: torch.Tensor, w: int, capacity: int | None = None, ctx: Context | None = None,

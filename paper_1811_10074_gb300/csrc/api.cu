@@ -174,6 +174,41 @@ sws_status sws_selftest_wait_timeout(sws_ctx *ctx, int which, void *stream) {
   return SWS_OK;
 }
 
+sws_status sws_selftest_minimizer_timeout(sws_ctx *ctx, uint64_t *count_out, void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  if (!count_out) return fail(SWS_ERR_INVALID, "count_out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // three tiles of k = 15, w = 10 windows over a zeroed scratch sequence in the workspace
+  const int k = 15, w = 10;
+  const uint64_t tiles = 3;
+  const uint64_t nwin = tiles * (uint64_t)sws::mini_tile_windows(w);
+  const uint64_t n = nwin + (uint64_t)(w + k - 1) - 1;
+  const uint64_t seq_bytes = round_up((n + 3) / 4, 256);
+  const MiniWs L = mini_ws_layout(tiles, seq_bytes);
+  s = ensure_ws(ctx, L.total, st);
+  if (s) return s;
+  char *ws = static_cast<char *>(ctx->ws);
+  SWS_CUDA(cudaMemsetAsync(ws, 0, L.tilebar_off, st));
+  SWS_CUDA(cudaMemsetAsync(ws + L.extra_off, 0, seq_bytes, st));
+  SWS_CUDA(cudaMemsetAsync(count_out, 0xff, sizeof(uint64_t), st));
+  sws::MiniArgs a{};
+  a.seq = reinterpret_cast<const uint8_t *>(ws + L.extra_off);
+  a.n = n;
+  a.k = k;
+  a.w = w;
+  a.mode = SWS_MINI_HASH;
+  a.count_out = count_out;
+  a.status = reinterpret_cast<unsigned long long *>(ws);
+  a.tile_counter = reinterpret_cast<unsigned int *>(ws + L.counter_off);
+  a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar_off);
+  a.err = ctx->d_err;
+  a.withhold_copy = 1;
+  cudaError_t e = sws::launch_minimizers_lookback(a, sws::SRC_DNA, sws::BAR_NBLOCK, tiles, st);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+  return SWS_OK;
+}
+
 sws_status sws_sliding_sum(sws_ctx *ctx, int op, int w, const void *in, void *out, uint64_t n, int variant,
                            void *stream) {
   sws_status s = enter(ctx);
@@ -369,8 +404,9 @@ sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrie
   if (staged) {
     const uint64_t tiles = (nwin + tw - 1) / tw;
     if (tiles >= 0xffffffffull) return fail(SWS_ERR_INVALID, "input too long");
-    const StagedWs L =
-        staged_ws_layout(tiles, (int)tw, sws::mini_fast_hash_bytes(source, a.k), barrier == sws::BAR_READS, extra);
+    // a count-only run needs no staging slots
+    const StagedWs L = staged_ws_layout(tiles, a.count_only ? 0 : (int)tw, sws::mini_fast_hash_bytes(source, a.k),
+                                        barrier == sws::BAR_READS, extra);
     sws_status s = ensure_ws(ctx, L.total, st);
     if (s) return s;
     char *w = static_cast<char *>(ctx->ws);
@@ -405,7 +441,7 @@ sws_status run_minimizers(sws_ctx *ctx, sws::MiniArgs &a, int source, int barrie
 static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq, const uint32_t *keys, uint64_t n,
                                     int k, int w, int mode, const int64_t *nblocks, uint64_t n_nblocks,
                                     void *hash_out, uint32_t *pos_out, uint64_t capacity, uint64_t *count_out,
-                                    void *stream) {
+                                    void *stream, bool count_only = false) {
   sws_status s = enter(ctx);
   if (s) return s;
   s = check_mini_args(k, w, mode);
@@ -436,6 +472,7 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
   a.pos_out = pos_out;
   a.capacity = capacity;
   a.count_out = count_out;
+  a.count_only = count_only ? 1 : 0;
   return run_minimizers(ctx, a, source, sws::BAR_NBLOCK, nwin, 0, nullptr, st);
 }
 
@@ -444,6 +481,94 @@ sws_status sws_minimizers(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, i
                           uint64_t capacity, uint64_t *count_out, void *stream) {
   return minimizers_common(ctx, sws::SRC_DNA, seq, nullptr, n, k, w, mode, nblocks, n_nblocks, hash_out, pos_out,
                            capacity, count_out, stream);
+}
+
+sws_status sws_minimizers_count(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                                const int64_t *nblocks, uint64_t n_nblocks, uint64_t *count_out, void *stream) {
+  return minimizers_common(ctx, sws::SRC_DNA, seq, nullptr, n, k, w, mode, nblocks, n_nblocks, nullptr, nullptr, 0,
+                           count_out, stream, /*count_only=*/true);
+}
+
+sws_status sws_build_table(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, int w, int mode,
+                           const int64_t *nblocks, uint64_t n_nblocks, int bucket_bits, void *sorted_hash,
+                           uint32_t *sorted_pos, uint64_t capacity, uint64_t *bucket_offsets, uint64_t *count,
+                           void *stream) {
+  sws_status s = enter(ctx);
+  if (s) return s;
+  s = check_mini_args(k, w, mode);
+  if (s) return s;
+  const int hash_bits = 2 * k;
+  if (bucket_bits < 0 || bucket_bits > hash_bits || bucket_bits > 32)
+    return fail(SWS_ERR_INVALID, "bucket_bits must be in [0, min(2k, 32)] (got %d)", bucket_bits);
+  if (!count || !bucket_offsets) return fail(SWS_ERR_INVALID, "count/bucket_offsets is NULL");
+  if (capacity > 0 && (!sorted_hash || !sorted_pos)) return fail(SWS_ERR_INVALID, "sorted_hash/sorted_pos is NULL");
+  *count = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // 1. the minimizers, written straight into the caller's output arrays (the sort's first pass
+  //    reads them and its last pass overwrites them; a one-pass sort, 2k <= 8, stages them in the
+  //    workspace first); the count goes to a word of the context's error block
+  uint64_t *d_count = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(ctx->d_err) + 128);
+  s = minimizers_common(ctx, sws::SRC_DNA, seq, nullptr, n, k, w, mode, nblocks, n_nblocks, sorted_hash, sorted_pos,
+                        capacity, d_count, stream);
+  if (s) return s;
+  uint64_t m = 0;
+  SWS_CUDA(cudaMemcpyAsync(&m, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  SWS_CUDA(cudaStreamSynchronize(st));
+  {
+    int err = 0;
+    SWS_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      SWS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+      return fail(SWS_ERR_TIMEOUT, "a bounded device-side wait ran out while finding the minimizers (bits 0x%x)", err);
+    }
+  }
+  *count = m;
+  if (m > capacity)
+    return fail(SWS_ERR_CAPACITY, "%llu minimizers exceed the capacity %llu", (unsigned long long)m,
+                (unsigned long long)capacity);
+  // 2. the seed table over the m hits, in place
+  const bool wide = hash_bits > 32;
+  const uint64_t hs = wide ? 8 : 4;
+  const bool one_pass = hash_bits <= 8;
+  const uint64_t kbytes = round_up(m * 8, 256), vbytes = wide ? round_up(m * 4, 256) : 0;
+  const uint64_t hbytes = round_up(sws::table_hist_words(m) * 4, 256);
+  const uint64_t bbytes = round_up(sws::table_bsum_words(m) * 4, 256);
+  const uint64_t gbytes = round_up(sws::table_gap_bytes(bucket_bits), 256);
+  const uint64_t copy_bytes = one_pass ? round_up(m * hs, 256) + round_up(m * 4, 256) : 0;
+  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256 + copy_bytes;
+  s = ensure_ws(ctx, total, st);
+  if (s) return s;
+  char *ws = static_cast<char *>(ctx->ws);
+  const void *in_hash = sorted_hash;
+  const uint32_t *in_pos = sorted_pos;
+  if (one_pass && m > 0) {
+    char *c = ws + total - copy_bytes;
+    SWS_CUDA(cudaMemcpyAsync(c, sorted_hash, m * hs, cudaMemcpyDeviceToDevice, st));
+    SWS_CUDA(cudaMemcpyAsync(c + round_up(m * hs, 256), sorted_pos, m * 4, cudaMemcpyDeviceToDevice, st));
+    in_hash = c;
+    in_pos = reinterpret_cast<const uint32_t *>(c + round_up(m * hs, 256));
+  }
+  sws::TableArgs a{};
+  a.hash = in_hash;
+  a.pos = in_pos;
+  a.m = m;
+  a.hash_bits = hash_bits;
+  a.bucket_bits = bucket_bits;
+  a.sorted_hash = sorted_hash;
+  a.sorted_pos = sorted_pos;
+  a.offsets = bucket_offsets;
+  a.ws_keys[0] = reinterpret_cast<unsigned long long *>(ws);
+  a.ws_keys[1] = reinterpret_cast<unsigned long long *>(ws + kbytes);
+  a.ws_vals[0] = wide ? reinterpret_cast<uint32_t *>(ws + 2 * kbytes) : nullptr;
+  a.ws_vals[1] = wide ? reinterpret_cast<uint32_t *>(ws + 2 * kbytes + vbytes) : nullptr;
+  a.ws_hist = reinterpret_cast<uint32_t *>(ws + 2 * kbytes + 2 * vbytes);
+  a.ws_bsum = reinterpret_cast<uint32_t *>(ws + 2 * kbytes + 2 * vbytes + hbytes);
+  a.ws_gaps = ws + 2 * kbytes + 2 * vbytes + hbytes + bbytes;
+  a.ws_ngaps = reinterpret_cast<unsigned long long *>(ws + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes);
+  a.gap_cap = sws::table_gap_capacity(bucket_bits);
+  cudaError_t e = sws::launch_table(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "seed-table launch");
+  return SWS_OK;
 }
 
 sws_status sws_minimizers_from_keys(sws_ctx *ctx, const uint32_t *keys, uint64_t m, int w, uint32_t *key_out,

@@ -80,6 +80,11 @@ struct MiniArgs {
   // time instead of from the fields above: one captured graph then serves any batch up to the
   // sizes it was built for.  Layout: see BatchDesc.
   const unsigned long long *desc;
+  // Failure self-test only: the look-back kernel announces its staging copies but never issues
+  // them, so every tile's bounded copy wait runs out.
+  int withhold_copy;
+  // Staged path: count the picks only (no staging area; the total goes to count_out).
+  int count_only;
 };
 
 // Device descriptor of a batch, read by the kernels of a captured batch graph.

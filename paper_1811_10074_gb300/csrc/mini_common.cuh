@@ -48,9 +48,10 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // Stage bytes [gb0, gb0 + sbytes) of the packed sequence into shared memory (zeros outside
 // [0, nbytes)).  The 16-byte-aligned interior goes by one TMA bulk copy completed on an
 // mbarrier; the ragged edge bytes are loaded by the threads.  Returns false (and records the
-// fault) if the copy did not complete within the spin limit.
+// fault) if the copy did not complete within the spin limit.  With issue = false the copy is
+// announced on the mbarrier but never started (the failure self-test: the wait then runs out).
 __device__ inline bool stage_bytes(uint8_t *sdst, const uint8_t *__restrict__ seq, uint64_t nbytes, long long gb0,
-                            int sbytes, unsigned long long *bar, int *err) {
+                            int sbytes, unsigned long long *bar, int *err, bool issue = true) {
   const long long lo = gb0 > 0 ? gb0 : 0;
   long long hi = gb0 + sbytes;
   if (hi > (long long)nbytes) hi = (long long)nbytes;
@@ -60,7 +61,7 @@ __device__ inline bool stage_bytes(uint8_t *sdst, const uint8_t *__restrict__ se
     mbar_init(bar, 1);
     fence_mbar_init();
     mbar_arrive_expect_tx(bar, (uint32_t)bulk);
-    bulk_g2s(sdst + (lo - gb0), seq + lo, (uint32_t)bulk, bar);
+    if (issue) bulk_g2s(sdst + (lo - gb0), seq + lo, (uint32_t)bulk, bar);
   }
   for (int b = threadIdx.x; b < sbytes; b += blockDim.x) {
     const long long g = gb0 + b;
@@ -194,11 +195,18 @@ struct KeyTraits<OpMinKey96> {
 };
 
 // Warp-level look-back (warp 0 of a CTA): 32 predecessors per poll.  Returns the number of picks
-// of all earlier tiles; sets `failed` if a wait ran out or an earlier tile failed.
+// of all earlier tiles; sets `failed` if a wait ran out or an earlier tile failed.  A tile that
+// failed itself (self_failed: its input never arrived) publishes the failure at once instead of a
+// count, so every later tile fails too and the final count is never written.
 __device__ inline unsigned long long lookback_warp(unsigned long long *status, uint32_t tile, unsigned long long agg,
-                                                   int *err, bool &failed) {
+                                                   int *err, bool &failed, bool self_failed = false) {
   const int lane = threadIdx.x & 31;
   failed = false;
+  if (self_failed) {
+    if (lane == 0) st_relaxed(&status[tile], FLAG_ERR);
+    failed = true;
+    return 0;
+  }
   if (tile == 0) {
     if (lane == 0) st_relaxed(&status[0], FLAG_INC | agg);
     return 0;

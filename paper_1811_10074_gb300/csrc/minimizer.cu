@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   bool ok = true;
   if (SRC == SRC_DNA) {
     if (t == 0) s_phase = (int)((unsigned long long)(ifirst + a.w) % (unsigned long long)a.w);
-    ok = stage_bytes(sbases, a.seq, (n + 3) / 4, p0 / 4 - 16, STAGE_BYTES_MINI, &s_mbar, a.err);
+    ok = stage_bytes(sbases, a.seq, (n + 3) / 4, p0 / 4 - 16, STAGE_BYTES_MINI, &s_mbar, a.err, !a.withhold_copy);
     const uint32_t *W = reinterpret_cast<const uint32_t *>(sbases);
     const int k = a.k;
     if (2 * k <= 32) {
@@ -244,6 +244,10 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
   HashT *sh_hash = reinterpret_cast<HashT *>(&sbc);
   uint32_t *sh_pos = reinterpret_cast<uint32_t *>(sh_hash + ML);
   uint32_t *sh_first = sh_pos + ML;  // staged read batches: read index of a read's first pick
+  if (STAGED && a.count_only) {
+    if (t == 0) a.tile_counts[tile] = total;
+    return;
+  }
   if (STAGED) {
     // stage the tile's picks in order in shared memory, then copy them to the tile's slot
     __syncthreads();  // the block-combine buffer is reused
@@ -274,9 +278,11 @@ __global__ void __launch_bounds__(MNT) k_minimizers(MiniArgs a, int TW, int span
     return;
   }
 
+  // a tile whose input copy timed out fails the ordered output (the count is never written)
+  const bool copy_failed = __syncthreads_or(!ok);
   if (warp == 0) {
     bool failed = false;
-    const unsigned long long ex = lookback_warp(a.status, tile, total, a.err, failed);
+    const unsigned long long ex = lookback_warp(a.status, tile, total, a.err, failed, copy_failed);
     if (lane == 0) {
       s_excl = ex;
       s_failed = failed ? 1 : 0;

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       if (i < warp) woff += c;
       total += c;
     }
-    {
+    if (!a.count_only) {
       uint32_t r = woff + inc - cnt;
 #pragma unroll
       for (int j = 0; j < VPT; ++j) {
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     }
     __syncthreads();
     const uint64_t slot = (uint64_t)tile * TW;
-    for (uint32_t i = t; i < total; i += FNT) {
+    for (uint32_t i = t; i < (a.count_only ? 0u : total); i += FNT) {
       static_cast<V *>(a.stg_hash)[slot + i] = sh_hash[i];
       a.stg_pos[slot + i] = sh_pos[i];
       if (BAR == BAR_READS) a.stg_first[slot + i] = sh_first[i];
@@ -614,6 +614,12 @@ __global__ void __launch_bounds__(GNT) k_mini_gather(MiniArgs a, uint32_t num_ti
       }
     }
   }
+}
+
+// Count-only runs: the total from the scanned per-tile counts.
+__global__ void k_mini_total(MiniArgs a, uint32_t num_tiles) {
+  if (a.desc) num_tiles = (uint32_t)a.desc[BD_TILES];
+  if (threadIdx.x == 0) *a.count_out = a.tile_counts[num_tiles];
 }
 
 template <int W, int BAR, int SRC, class V>
@@ -706,6 +712,10 @@ cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier,
   if (a.desc) e = scan_u32_dev(a.tile_counts, num_tiles + 1, a.desc + BD_SCAN_LEN, a.scan_tmp, st);
   else e = scan_u32(a.tile_counts, num_tiles + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
+  if (a.count_only) {
+    k_mini_total<<<1, 32, 0, st>>>(a, (uint32_t)num_tiles);
+    return cudaGetLastError();
+  }
   const unsigned blocks = (unsigned)(num_tiles < (1u << 20) ? num_tiles : (1u << 20));
   if (barrier == BAR_READS) {
     if (k64) k_mini_gather<BAR_READS, U64><<<blocks, GNT, 0, st>>>(a, (uint32_t)num_tiles, TW);

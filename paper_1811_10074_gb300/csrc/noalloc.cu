@@ -10,10 +10,14 @@
 // declares in device global memory; a call allocates nothing and needs no context.
 //
 // The array lives as long as the library is loaded, on every device that loads it (4 MiB each).
-// Its device address is looked up once per device (cudaGetSymbolAddress, with that device
-// current) on the first call made on that device; host code never passes the symbol itself.
+// Its device address is looked up (cudaGetSymbolAddress, with that device current) on the first
+// call made in each CUDA context of a device and kept for that context: a device reset or a new
+// primary context reloads the module at another address, so the cached address is keyed on the
+// context handle, never reused across contexts.  Host code never passes the symbol itself.
 #include <cstdio>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/sws.h"
 #include "internal.h"
@@ -29,26 +33,61 @@ namespace {
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {};
+struct Cached {
+  CUcontext ctx;       // the context the address belongs to
+  unsigned char *addr;
+};
+Cached g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up on first use).
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+
+// cuCtxGetCurrent from the driver, looked up once through the runtime (no -lcuda).
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = []() -> CtxGetCurrent {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<CtxGetCurrent>(p);
+    return nullptr;
+  }();
+  return fn;
+}
+
+// Device address of the scratch array in the current context of the current device (set up on
+// the first call in that context).
 int scratch_address(unsigned char **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return sws::report_error(SWS_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return sws::report_error(SWS_ERR_UNSUPPORTED, "device index too large");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  CtxGetCurrent get = ctx_get_current();
+  if (!get) return sws::report_error(SWS_ERR_CUDA, "cuCtxGetCurrent is not available");
+  auto lookup = [](unsigned char **addr) -> int {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, sws_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
+    const cudaError_t le = cudaGetSymbolAddress(&p, sws_noalloc_scratch);
+    if (le != cudaSuccess || !p) {
       char msg[256];
-      snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the fixed scratch failed: %s", cudaGetErrorString(e));
+      snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the fixed scratch failed: %s", cudaGetErrorString(le));
       return sws::report_error(SWS_ERR_CUDA, msg);
     }
-    g_addr[dev] = static_cast<unsigned char *>(p);
+    *addr = static_cast<unsigned char *>(p);
+    return SWS_OK;
+  };
+  std::lock_guard<std::mutex> lock(g_mu);
+  CUcontext cur = nullptr;
+  if (get(&cur) != CUDA_SUCCESS) return sws::report_error(SWS_ERR_CUDA, "cuCtxGetCurrent failed");
+  if (cur != nullptr && g_addr[dev].ctx == cur && g_addr[dev].addr) {
+    *out = g_addr[dev].addr;
+    return SWS_OK;
   }
-  *out = g_addr[dev];
+  // first call in this context (the lookup also makes the runtime set the context up)
+  unsigned char *addr = nullptr;
+  const int s = lookup(&addr);
+  if (s) return s;
+  if (get(&cur) != CUDA_SUCCESS || !cur) return sws::report_error(SWS_ERR_CUDA, "no current CUDA context");
+  g_addr[dev] = Cached{cur, addr};
+  *out = addr;
   return SWS_OK;
 }
 

@@ -573,8 +573,8 @@ def check_batch_and_keys(lib):
     assert int(po[-1]) == cur == len(h)
     keys = rng.integers(0, 1 << 30, size=500, dtype=np.uint64)
     keys[100:140] = 5  # a run of equal keys: the leftmost must win
-    for w in (1, 4, 17):
-        kh, kp = O.minimizers_from_keys(keys, w, lib=lib)
+    keys[300:330] = rng.integers(0, 3, size=30)  # few distinct values: ties everywhere
+    for w in (1, 2, 4, 10, 17):
         exp = []
         last = None
         for q in range(500 - w + 1):
@@ -582,7 +582,9 @@ def check_batch_and_keys(lib):
             if j != last:
                 exp.append((int(keys[j]), j))
             last = j
-        assert list(zip((int(v) for v in kh), (int(v) for v in kp))) == exp
+        for deque in (False, True):  # the naive scan ("Array") and the queue ("Dequeue") of Sec. 4
+            kh, kp = O.minimizers_from_keys(keys, w, deque=deque, lib=lib)
+            assert list(zip((int(v) for v in kh), (int(v) for v in kp))) == exp, (w, deque)
 
 
 def check_table(lib):

@@ -47,3 +47,29 @@ def test_selftest_rejects_unknown_wait():
             B._check(B.load().sws_selftest_wait_timeout(ctx.handle, 7, None))
     finally:
         ctx.close()
+
+
+def test_minimizer_copy_timeout_leaves_count_all_ones():
+    """The look-back minimizer kernel (the path of small sws_minimizers calls and of
+    sws_minimizers_noalloc) with its input copies withheld: each tile's bounded copy wait runs
+    out, the tile publishes a failure instead of its count, and no tile writes the total."""
+    ctx = B.Context(0)
+    try:
+        ctx.sync()
+        t0 = time.perf_counter()
+        cnt = B.selftest_minimizer_timeout(ctx=ctx)
+        with pytest.raises(B.SwsError, match="TIMEOUT"):
+            ctx.sync()
+        assert time.perf_counter() - t0 < 30.0
+        assert int(cnt.item()) == -1  # all ones: the ordered output was not completed
+        ctx.sync()
+        from paper_1811_10074_gb300 import synth
+        import oracle
+        n = 20_000
+        seq = synth.acgt_uniform_packed(n, seed=3)
+        h, p = B.minimizers(seq.cuda(), n, 15, 10, ctx=ctx)
+        want_h, want_p = oracle.minimizers(seq, n, 15, 10)
+        assert np.array_equal(p.cpu().numpy().view(np.uint32), want_p)
+        assert np.array_equal(h.cpu().numpy().view(np.uint32).astype(np.uint64), want_h)
+    finally:
+        ctx.close()

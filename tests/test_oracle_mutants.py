@@ -77,6 +77,14 @@ MUTANTS = [
      "while (tail > head && key[dq[tail - 1]] > key[j]) tail--;",
      "while (tail > head && key[dq[tail - 1]] >= key[j]) tail--;",
      [pins.check_minimizers_bruteforce]),
+    ("keys_deque_pops_equal_keys",
+     "while (back > front && key[q[back - 1]] > key[i]) back--;",
+     "while (back > front && key[q[back - 1]] >= key[i]) back--;",
+     [pins.check_batch_and_keys]),
+    ("keys_deque_dedup_by_value",
+     "if (!have_prev || q[front] != prev) sink_put(&o, key[q[front]], q[front]);",
+     "if (!have_prev || key[q[front]] != key[prev]) sink_put(&o, key[q[front]], q[front]);",
+     [pins.check_batch_and_keys]),
     ("table_offsets_unshifted",
      "offsets[(t[i].h >> shift) + 1]++;",
      "offsets[(t[i].h >> shift)]++;",
