@@ -60,7 +60,10 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (AUTO uses its fixed rule)")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
-    ap.add_argument("--section", default="all", choices=["all", "sliding", "minimizers", "table", "batch", "serve"],
+    ap.add_argument("--keys-n", type=int, default=1 << 28, help="keys of the --section keys measurement")
+    ap.add_argument("--keys-ws", default="4,5,6,7,8,9,10,11,12,13,14,15,16,17", help="window lengths of --section keys")
+    ap.add_argument("--section", default="all",
+                    choices=["all", "sliding", "minimizers", "keys", "table", "batch", "serve"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
@@ -467,19 +470,7 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     # genome, 2^28 of them (sws_kmers with the hash), w = 10 and the sweep w = 4..17 (the window
     # lengths of the paper's timing figure)
     m = 1 << 28
-    gseq = synth.acgt_uniform_packed(m + 14, seed=44, device=dev)
-    keys = P.kmers(gseq, m + 14, 15, "hash", ctx=ctx, stream=stream)
-    del gseq
-    sweep = {}
-    for w in range(4, 18):
-        cap = int(m * 2.6 / (w + 1)) + 1024
-        ms = time_call(lambda: P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False), 5,
-                       stream)
-        _, _, cnt = P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
-        picks = int(cnt.item())
-        b = 4 * m + 8 * picks
-        sweep[w] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
-                    "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    keys, sweep = keys_sweep(dev, ctx, m, range(4, 18))
     out["sliding_min_keys_2^28_w10"] = sweep[10]
     out["sliding_min_keys_2^28_w4_17"] = {str(w): {"ms": v["ms"], "gbs": v["gbs"], "frac_hbm": v["frac_hbm"]}
                                           for w, v in sweep.items()}
@@ -487,6 +478,32 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     if with_cpu:
         out["cpu_baseline"] = minimizer_cpu_baseline(keys, m, sweep)
     return out
+
+
+def keys_sweep(dev, ctx, m: int, ws, reps: int = 5):
+    """The sliding minimum with deduplicated picks over m hashed canonical 15-mers of a uniform
+    sequence (seed 44) for each w in ws: ms per call (CUDA events over `reps` calls), GB/s of the
+    algorithmic bytes (4 B per key in, 8 B per pick out) and their fraction of the measured HBM
+    bandwidth.  Returns (keys, {w: figures})."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    peak, _ = measured_peaks()
+    gseq = synth.acgt_uniform_packed(m + 14, seed=44, device=dev)
+    keys = P.kmers(gseq, m + 14, 15, "hash", ctx=ctx, stream=stream)
+    del gseq
+    sweep = {}
+    for w in ws:
+        cap = int(m * 2.6 / (w + 1)) + 1024
+        ms = time_call(lambda: P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False), reps,
+                       stream)
+        _, _, cnt = P.minimizers_from_keys(keys, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
+        picks = int(cnt.item())
+        b = 4 * m + 8 * picks
+        sweep[w] = {"ms": round(ms, 3), "gbs": round(b / (ms / 1e3) / 1e9, 1),
+                    "frac_hbm": round(b / (ms / 1e3) / 1e9 / peak, 4), "picks": picks}
+    ctx.sync(stream)
+    return keys, sweep
 
 
 def minimizer_cpu_baseline(keys, m, sweep, sample_keys: int = 1 << 24, sample_bases: int = 1 << 22):
@@ -775,14 +792,18 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section in ("minimizers", "table", "batch", "serve"):
+    if args.section in ("minimizers", "keys", "table", "batch", "serve"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
         dev = torch.device("cuda", torch.cuda.current_device())
         ctx = P.default_context(dev.index)
         if rank == 0:
-            if args.section == "minimizers":
+            if args.section == "keys":
+                ws = [int(v) for v in args.keys_ws.split(",") if v]
+                _, sweep = keys_sweep(dev, ctx, args.keys_n, ws)
+                print(json.dumps({"keys": {"n": args.keys_n, "sweep": sweep}}), flush=True)
+            elif args.section == "minimizers":
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n, with_cpu=not args.no_cpu)}), flush=True)
             elif args.section == "table":
                 print(json.dumps({"genome_table": genome_table_extras(dev, ctx, args.genome_n)}), flush=True)

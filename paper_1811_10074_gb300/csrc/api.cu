@@ -459,6 +459,15 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
   }
   if (source == sws::SRC_DNA && !seq) return fail(SWS_ERR_INVALID, "seq is NULL");
   if (source == sws::SRC_KEYS && !keys) return fail(SWS_ERR_INVALID, "keys is NULL");
+  if (source == sws::SRC_KEYS && !count_only && sws::keys_min_applies(keys, n, w)) {
+    // w <= 17: the single-pass kernel of keys_min.cu
+    s = ensure_ws(ctx, sws::keys_min_ws_bytes(n, w), st);
+    if (s) return s;
+    cudaError_t e = sws::launch_keys_min(keys, n, w, static_cast<uint32_t *>(hash_out), pos_out, capacity, count_out,
+                                         ctx->ws, ctx->d_err, ctx->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "key minimizer launch");
+    return SWS_OK;
+  }
   sws::MiniArgs a{};
   a.seq = seq;
   a.keys = keys;

@@ -113,6 +113,14 @@ int mini_fast_tile_windows(int w);
 cudaError_t launch_minimizers_staged(const MiniArgs &a, int source, int barrier, uint64_t num_tiles,
                                      cudaStream_t stream);
 
+// Sliding minimum over precomputed keys for w <= 17 (keys_min.cu): one pass, picks placed in
+// order by per-tile counts.  Needs keys aligned to 16 bytes and at least 32 of them.
+bool keys_min_applies(const uint32_t *keys, uint64_t m, int w);
+uint64_t keys_min_ws_bytes(uint64_t m, int w);  // workspace (zeroed by the launcher)
+cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *key_out, uint32_t *pos_out,
+                            uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
+                            cudaStream_t stream);
+
 // The per-tile summary of the barriers (N-blocks or read starts) that can touch each tile.
 bool tile_barriers_needed(const MiniArgs &a, int source, int barrier);
 cudaError_t launch_tile_barriers(const MiniArgs &a, int source, int barrier, uint64_t num_tiles, int TW, int span,

@@ -1,0 +1,699 @@
+// keys_min.cu -- the paper's timed task (Sec. 4) on the GPU: the deduplicated sliding minimum of
+// a precomputed key array (Eq. 2 with (+) = min over keys ordered by (value, position), picks of
+// consecutive windows stored once, Sec. 2.4), for windows of w = 1..17 keys, in ONE pass over the
+// keys with the picks written in position order.
+//
+// Tiles.  A tile is 4096 consecutive windows; thread t of the 256-thread CTA owns windows
+// 16t .. 16t+15 of the tile and reads keys 16t .. 16t+w+14 of it (its own 16 and the first w-1 of
+// the next thread's).  A tile's keys arrive in shared memory by one 2-D TMA copy of 130 rows of
+// 128 bytes (the key array viewed as rows of 32 keys): the row before the tile (its last key
+// decides whether the tile's first window stores a pick), the tile's 128 rows, and the row after
+// (the halo of the last windows).  The 128-byte swizzle puts 16-byte unit u of shared row r at
+// unit u ^ (r & 7), so each quarter-warp's 16-byte reads fall in distinct bank groups.  Keys of
+// a final partial row are not in the tensor map; the threads that need them load them directly.
+//
+// Window minima.  Blocks of w keys aligned at the thread's first key: window j is the suffix of
+// block j/w from j combined with the prefix of the next block up to j+w-1 (the block combine of
+// Eq. 2 with blocks of exactly w, van Herk / Gil-Werman), about three compares per window, all in
+// registers.  Keys compare by value and carry their position (a compile-time constant): a suffix
+// step takes an equal key (the left one), a prefix step does not, and the suffix part wins ties
+// against the prefix part, so every window knows its leftmost least key.  A window stores a pick
+// when its pick's position differs from the previous window's.
+//
+// Order.  Tiles are handed out by an atomic ticket, in order, and each CTA takes its tickets in
+// increasing order.  A tile's pick count goes to its status word as soon as it is known; the
+// tile's picks wait in shared memory while the CTA computes its next tile, and then the CTA finds
+// their output offset as the end of its own previous tile's picks plus the counts of all tiles
+// between the two -- published by now, since each is published right after it is computed and
+// every ticket below this one is held by a running CTA.  That costs each thread one or two reads
+// of hot status words per tile; there is no staging area, no second pass, no inclusive-prefix
+// chain.  Every wait is bounded: a wait that runs out records the fault, the CTA publishes a
+// failure mark instead of its later counts, and every tile after it then fails as well (its
+// offset would include a missing count), so the final count is never written.
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/sws.h"
+#include "common.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace sws {
+
+namespace {
+
+constexpr int KNT = 256;                  // threads per CTA
+constexpr int KWPT = 16;                  // windows per thread
+constexpr int KTILE = KNT * KWPT;         // windows per tile
+constexpr int KMAXW = 17;                 // the largest w: a thread's keys fit in 32 registers
+constexpr int KROWS = KTILE / 32 + 2;     // rows per stage: the row before, 128, the row after
+constexpr int KSTAGE_BYTES = KROWS * 128; // bytes one copy brings
+constexpr int KSTAGE_STRIDE = (KSTAGE_BYTES + 1023) / 1024 * 1024;  // 1024-aligned for the swizzle
+constexpr int KSTAGES = 3;
+constexpr int KSLOTS = 3;                 // pick slots: a tile is placed two tiles after it is counted
+constexpr int KCAP = 2560;                // picks a slot holds (more: the tile is placed at once)
+constexpr size_t KSMEM = 1024 + (size_t)KSTAGES * KSTAGE_STRIDE + (size_t)KSLOTS * KCAP * 8;
+constexpr uint32_t ST_DONE = 0x80000000u;  // status: count published (low bits)
+constexpr uint32_t ST_FAIL = 0xC0000000u;  // status: the tile failed
+constexpr uint32_t ST_COUNT = 0x3FFFFFFFu;
+
+// Workspace header of one launch (zeroed with the status words).
+struct KeysHeader {
+  unsigned int ticket;  // next tile
+  unsigned int done;    // CTAs that have finished
+  unsigned int fail;    // nonzero: some CTA failed
+  unsigned int pad;
+  unsigned long long total;  // picks of all tiles (written when the last tile is placed)
+};
+
+struct KeysArgs {
+  const uint32_t *keys;
+  uint64_t m;          // keys
+  uint64_t n_full;     // keys in whole 32-key rows (the tensor map's extent)
+  uint64_t nwin;       // windows = m - w + 1
+  uint32_t num_tiles;
+  uint32_t *status;    // one word per tile, zeroed before the launch
+  KeysHeader *hdr;     // zeroed before the launch
+  uint32_t *key_out;
+  uint32_t *pos_out;
+  uint64_t capacity;
+  uint64_t *count_out;
+  int *err;
+  int vec_ok;  // key_out and pos_out are 16-byte aligned at the same phase (vector stores)
+};
+
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Byte offset in a stage of tile-local key q (q = -32 .. KTILE + 31): shared row 1 + q/32 (row 0
+// holds the keys before the tile), 16-byte unit swizzled by the row.
+__device__ __forceinline__ int stage_offset(int q) {
+  const int s = q + 32, row = s >> 5, col = s & 31;
+  return row * 128 + ((((col >> 2) ^ (row & 7))) << 4) + ((col & 3) << 2);
+}
+
+// Minimum of every window j = 0..15 of a thread (keys X[j .. j+W-1]) and the thread-relative
+// position of its leftmost least key, by blocks of W aligned at X[0].
+template <int W>
+__device__ __forceinline__ void window_minima(const uint32_t (&X)[32], uint32_t (&mv)[KWPT], int (&mp)[KWPT]) {
+  constexpr int NK = KWPT + W - 1;
+  // suffix minima of the blocks that hold a window start (equal keys: the left one)
+  uint32_t Sv[KWPT];
+  int Sp[KWPT];
+#pragma unroll
+  for (int b = 0; b * W < KWPT; ++b) {
+    const int lo = b * W, hi = b * W + W - 1;  // hi <= NK - 1
+    uint32_t v = X[hi];
+    int p = hi;
+    if (hi < KWPT) {
+      Sv[hi] = v;
+      Sp[hi] = p;
+    }
+#pragma unroll
+    for (int i = hi - 1; i >= lo; --i) {
+      if (X[i] <= v) {
+        v = X[i];
+        p = i;
+      }
+      if (i < KWPT) {
+        Sv[i] = v;
+        Sp[i] = p;
+      }
+    }
+  }
+  // prefix minima of the blocks that hold a window end j + W - 1 of a window j that is not a
+  // block start (equal keys: the earlier one stays)
+  uint32_t Pv[NK];
+  int Pp[NK];
+#pragma unroll
+  for (int b = 1; b * W <= KWPT + W - 2; ++b) {
+    const int lo = b * W;
+    const int hi = lo + W - 2 < NK - 1 ? lo + W - 2 : NK - 1;
+    uint32_t v = X[lo];
+    int p = lo;
+    Pv[lo] = v;
+    Pp[lo] = p;
+#pragma unroll
+    for (int i = lo + 1; i <= hi; ++i) {
+      if (X[i] < v) {
+        v = X[i];
+        p = i;
+      }
+      Pv[i] = v;
+      Pp[i] = p;
+    }
+  }
+  // window = suffix part (left) + prefix part (right); the left part wins ties
+#pragma unroll
+  for (int j = 0; j < KWPT; ++j) {
+    if (j % W == 0) {
+      mv[j] = Sv[j];
+      mp[j] = Sp[j];
+    } else {
+      const int e = j + W - 1;
+      const bool c = Sv[j] <= Pv[e];
+      mv[j] = c ? Sv[j] : Pv[e];
+      mp[j] = c ? Sp[j] : Pp[e];
+    }
+  }
+}
+
+// Thread-relative position of the pick of the window just before the thread's first (keys
+// xm1 = X[-1], X[0 .. W-2]).
+template <int W>
+__device__ __forceinline__ int prev_window_pick(uint32_t xm1, const uint32_t (&X)[32]) {
+  uint32_t v = xm1;
+  int p = -1;
+#pragma unroll
+  for (int i = 0; i < W - 1; ++i)
+    if (X[i] < v) {
+      v = X[i];
+      p = i;
+    }
+  return p;
+}
+
+
+// This thread's share of the counts of tiles lo .. hi-1, polling (bounded) any not yet published.
+// bad: bit 0 = a tile failed, bit 1 = a count was not published within the wait bound.
+__device__ __forceinline__ unsigned long long partial_counts(const uint32_t *status, long long lo, long long hi,
+                                                             int &bad) {
+  unsigned long long sum = 0;
+  for (long long j = lo + threadIdx.x; j < hi; j += KNT) {
+    uint32_t v = ld_relaxed_u32(&status[j]);
+    if (!(v & ST_DONE)) {
+      const unsigned long long t0 = tma::now_ns();
+      while (!(v & ST_DONE)) {
+        if (tma::now_ns() - t0 > tma::kWaitNs) {
+          bad |= 2;
+          break;
+        }
+        __nanosleep(100);
+        v = ld_relaxed_u32(&status[j]);
+      }
+    }
+    if ((v & ST_FAIL) == ST_FAIL) bad |= 1;
+    sum += v & ST_COUNT;
+  }
+  return sum;
+}
+
+// Wait (bounded) until status word *p, last read as v, is published; returns it.
+__device__ __forceinline__ uint32_t await_status(const uint32_t *p, uint32_t v, int &bad) {
+  if (!(v & ST_DONE)) {
+    v = ld_relaxed_u32(p);
+    const unsigned long long t0 = tma::now_ns();
+    while (!(v & ST_DONE)) {
+      if (tma::now_ns() - t0 > tma::kWaitNs) {
+        bad |= 2;
+        break;
+      }
+      __nanosleep(100);
+      v = ld_relaxed_u32(p);
+    }
+  }
+  if ((v & ST_FAIL) == ST_FAIL) bad |= 1;
+  return v;
+}
+
+// The same summed over the CTA (barriers inside; every thread gets the total and the bad bits).
+__device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status, long long lo, long long hi, int &bad,
+                                                         unsigned long long *red, int *flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int b = 0;
+  unsigned long long sum = partial_counts(status, lo, hi, b);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(kFull, sum, d);
+  b = (int)__reduce_or_sync(kFull, (unsigned)b);
+  __syncthreads();  // the scratch may still be read from its last use
+  if (lane == 0) {
+    red[warp] = sum;
+    flag[warp] = b;
+  }
+  __syncthreads();
+  sum = 0;
+  b = 0;
+#pragma unroll
+  for (int i = 0; i < KNT / 32; ++i) {
+    sum += red[i];
+    b |= flag[i];
+  }
+  bad |= b;
+  return sum;
+}
+
+// Copy a placed tile's picks from its slot to the output (keys, positions), coalesced: after up to
+// three single picks that reach a 16-byte boundary of the output, four picks per thread and
+// store (two 16-byte stores), then the tail.  When the picks run past the capacity, or the two
+// output arrays are not both 16-byte aligned at the same phase, one pick per thread and store.
+__device__ __forceinline__ void write_slot(const uint2 *slot, uint32_t cnt, uint32_t tile, unsigned long long base,
+                                           const KeysArgs &a) {
+  const uint32_t pos0 = tile * (uint32_t)KTILE;
+  if (a.vec_ok && base + cnt <= a.capacity) {
+    uint32_t *ko = a.key_out + base;
+    uint32_t *po = a.pos_out + base;
+    const uint32_t head = (uint32_t)(((16u - (reinterpret_cast<uintptr_t>(ko) & 15u)) & 15u) >> 2);
+    const uint32_t h = head < cnt ? head : cnt;
+    const uint32_t nq = (cnt - h) >> 2;
+    if (threadIdx.x < h) {
+      const uint2 pk = slot[threadIdx.x];
+      ko[threadIdx.x] = pk.x;
+      po[threadIdx.x] = pos0 + pk.y;
+    }
+    for (uint32_t q = threadIdx.x; q < nq; q += KNT) {
+      const uint32_t x = h + 4 * q;
+      const uint2 p0 = slot[x], p1 = slot[x + 1], p2 = slot[x + 2], p3 = slot[x + 3];  // 8-byte aligned
+      *reinterpret_cast<uint4 *>(ko + x) = make_uint4(p0.x, p1.x, p2.x, p3.x);
+      *reinterpret_cast<uint4 *>(po + x) = make_uint4(pos0 + p0.y, pos0 + p1.y, pos0 + p2.y, pos0 + p3.y);
+    }
+    const uint32_t x = h + 4 * nq + threadIdx.x;
+    if (x < cnt) {
+      const uint2 pk = slot[x];
+      ko[x] = pk.x;
+      po[x] = pos0 + pk.y;
+    }
+    return;
+  }
+  for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
+    const uint2 pk = slot[x];
+    const unsigned long long gi = base + x;
+    if (gi < a.capacity) {
+      a.key_out[gi] = pk.x;
+      a.pos_out[gi] = pos0 + pk.y;
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUtensorMap tmap, KeysArgs a) {
+  extern __shared__ __align__(16) unsigned char ksm_raw[];
+  __shared__ __align__(8) unsigned long long s_bar[KSTAGES];
+  __shared__ uint32_t s_tk[KSTAGES];
+  __shared__ int s_issued[KSTAGES];  // a copy was issued into the stage and not yet waited for
+  // per iteration parity, per warp: its pick count, failure bits, and its share of the counts
+  // before the tile being placed (every sum of pick counts is below 2^32: picks <= keys < 2^32)
+  __shared__ uint4 s_sum[2][KNT / 32];
+  __shared__ unsigned long long s_red_sync[KNT / 32];
+  __shared__ int s_flag_sync[KNT / 32];
+  unsigned char *stages = ksm_raw + ((1024u - (tma::smem_u32(ksm_raw) & 1023u)) & 1023u);
+  uint2 *slots = reinterpret_cast<uint2 *>(stages + KSTAGES * KSTAGE_STRIDE);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t T = a.num_tiles;
+  constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+  auto issue = [&](int s, uint32_t tile) {  // thread 0: rows 128 tile - 1 .. 128 tile + 128
+    tma::mbar_arrive_expect_tx(&s_bar[s], KSTAGE_BYTES);
+    tma::tensor_g2s_2d(stages + s * KSTAGE_STRIDE, &tmap, 0, (int)(tile * (KTILE / 32)) - 1, &s_bar[s]);
+  };
+  auto set_failed = [&](bool &failed, int why) {  // uniform; thread 0 records the cause
+    if (!failed && t == 0) {
+      if (why) atomicOr(a.err, why);
+      atomicOr(&a.hdr->fail, 1u);
+    }
+    failed = true;
+  };
+  if (t == 0) {
+    tma::prefetch_tensormap(&tmap);
+#pragma unroll
+    for (int s = 0; s < KSTAGES; ++s) tma::mbar_init(&s_bar[s], 1);
+    tma::fence_mbar_init();
+#pragma unroll
+    for (int s = 0; s < KSTAGES; ++s) {
+      const uint32_t tk = atomicAdd(&a.hdr->ticket, 1u);
+      s_tk[s] = tk;
+      s_issued[s] = tk < T;
+      if (tk < T) issue(s, tk);
+    }
+  }
+  // thread 0 holds one ticket beyond the stages, taken a tile early so that the atomic's round
+  // trip is not on the path of a refill
+  uint32_t spare = t == 0 ? atomicAdd(&a.hdr->ticket, 1u) : 0u;
+  __syncthreads();
+
+  uint32_t phases = 0;             // bit s: parity of stage s's next completion
+  long long run_tile = -1;         // the last tile whose picks were placed ...
+  unsigned long long run_end = 0;  // ... and the end of its picks in the output
+  // tiles counted but not yet placed (at most KSLOTS - 1), oldest first, with their slots
+  int L = 0;
+  uint32_t pt0 = NONE, pt1 = NONE, pc0 = 0, pc1 = 0;
+  int ps0 = 0, ps1 = 0;
+  uint32_t pushes = 0;  // tiles deferred so far: the next one goes to slot pushes % KSLOTS
+  bool failed = false;  // uniform across the CTA
+  // this thread's 16-byte units in a stage, the same for every tile: its own keys q0 .. q0+15 in
+  // shared row 1 + t/2, units 4 (t&1) .. +3, and the next thread's first keys in the same row
+  // (t even, units 4..7) or the next row (units 0..3); a unit u of row r sits at u ^ (r & 7)
+  const int q0 = t * KWPT;
+  const int row_a = 1 + (t >> 1), row_b = row_a + (t & 1);
+  const int base_a = row_a * 128 + ((((t & 1) * 4) ^ (row_a & 4)) << 4), r3a = row_a & 3;
+  const int base_b = row_b * 128 + (((t & 1 ? 0 : 4) ^ (row_b & 4)) << 4), r3b = row_b & 3;
+  for (int it = 0;; ++it) {
+    const int s = it % KSTAGES, par = it & 1;
+    const uint32_t tile = s_tk[s];
+    if (tile >= T) break;
+    // ---- this tile's keys (each thread waits for the copy itself) ---------------------------------
+    const bool issued = s_issued[s] != 0 && !failed;  // a failed CTA waits for its copies at exit
+    // the counts before the oldest deferred tile (placed after this tile's barrier): two status
+    // words per thread read now, so that the round trip overlaps this tile's work
+    const bool pop = L == KSLOTS - 1 && !failed;
+    const long long j0 = run_tile + 1 + t;
+    uint32_t sv0 = 0, sv1 = 0;
+    if (pop && j0 < (long long)pt0) sv0 = ld_relaxed_u32(&a.status[j0]);
+    if (pop && j0 + KNT < (long long)pt0) sv1 = ld_relaxed_u32(&a.status[j0 + KNT]);
+    const bool ok = issued && tma::mbar_wait_bounded(&s_bar[s], (phases >> s) & 1u);
+    const bool wok = __all_sync(kFull, ok);
+    const uint64_t tb = (uint64_t)tile * KTILE;  // first window (and key) of the tile
+    const uint64_t g0 = tb + (uint64_t)q0;      // this thread's first window
+    uint32_t mv[KWPT];
+    int mp[KWPT];
+    unsigned mask = 0;  // windows that store a pick
+    if (wok) {
+      const unsigned char *st = stages + s * KSTAGE_STRIDE;
+      uint32_t X[32];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(st + base_a + ((c ^ r3a) << 4));
+        X[4 * c] = u.x;
+        X[4 * c + 1] = u.y;
+        X[4 * c + 2] = u.z;
+        X[4 * c + 3] = u.w;
+      }
+      constexpr int NU = (W - 1 + 3) / 4;  // 16-byte units of the next thread's keys needed
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < NU) {
+          const uint4 u = *reinterpret_cast<const uint4 *>(st + base_b + ((c ^ r3b) << 4));
+          X[16 + 4 * c] = u.x;
+          X[16 + 4 * c + 1] = u.y;
+          X[16 + 4 * c + 2] = u.z;
+          X[16 + 4 * c + 3] = u.w;
+        } else {
+          X[16 + 4 * c] = X[16 + 4 * c + 1] = X[16 + 4 * c + 2] = X[16 + 4 * c + 3] = 0xFFFFFFFFu;
+        }
+      }
+      uint32_t xm1 = lane == 0 ? *reinterpret_cast<const uint32_t *>(st + stage_offset(q0 - 1)) : 0u;
+      if (g0 + KWPT + W - 1 > a.n_full) {  // keys of the final partial row (or past the end)
+#pragma unroll
+        for (int i = 0; i < KWPT + W - 1; ++i) {
+          const uint64_t gi = g0 + (uint64_t)i;
+          if (gi >= a.n_full) X[i] = gi < a.m ? a.keys[gi] : 0xFFFFFFFFu;
+        }
+        if (lane == 0 && g0 >= 1 && g0 - 1 >= a.n_full && g0 - 1 < a.m) xm1 = a.keys[g0 - 1];
+      }
+      window_minima<W>(X, mv, mp);
+      // the pick of the window before this thread's first: the previous lane's last, shifted to
+      // this thread's frame; lane 0 of each warp finds it from its own keys
+      int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
+      if (lane == 0) pp = g0 == 0 ? -1000 : prev_window_pick<W>(xm1, X);
+      // windows that store a pick: a pick other than the window before's, inside the sequence
+#pragma unroll
+      for (int j = 0; j < KWPT; ++j) {
+        mask |= (unsigned)(mp[j] != pp) << j;
+        pp = mp[j];
+      }
+      const long long left = (long long)a.nwin - (long long)g0;
+      if (left < KWPT) mask &= left <= 0 ? 0u : ((1u << left) - 1u);
+    }
+    const uint32_t cnt = __popc(mask);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += u;
+    }
+    // the counts before the oldest deferred tile, placed below once the barrier has summed them
+    int bad = 0;
+    uint32_t part = 0;
+    if (pop) {
+      if (j0 < (long long)pt0) part += await_status(&a.status[j0], sv0, bad) & ST_COUNT;
+      if (j0 + KNT < (long long)pt0) part += await_status(&a.status[j0 + KNT], sv1, bad) & ST_COUNT;
+      if (run_tile + 1 + 2 * KNT < (long long)pt0)  // a long gap (rare): the rest
+        part += (uint32_t)partial_counts(a.status, run_tile + 1 + 2 * KNT, pt0, bad);
+    }
+    part = __reduce_add_sync(kFull, part);
+    bad = (int)__reduce_or_sync(kFull, (unsigned)(bad | (issued && !wok ? 4 : 0)));
+    if (lane == 31) s_sum[par][warp] = make_uint4(inc, (uint32_t)bad, part, 0u);
+    __syncthreads();  // the one barrier of a tile
+    // lane i reads warp i's summary; sums and this warp's offset by shuffles
+    const uint4 v = lane < KNT / 32 ? s_sum[par][lane] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t tot = __reduce_add_sync(kFull, v.x);
+    const int flags = (int)__reduce_or_sync(kFull, v.y);
+    const unsigned long long between = __reduce_add_sync(kFull, v.z);
+    uint32_t wi = v.x;
+#pragma unroll
+    for (int d = 1; d < KNT / 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, wi, d);
+      if (lane >= d) wi += u;
+    }
+    const uint32_t woff = __shfl_sync(kFull, wi - v.x, warp);
+    if (issued) {
+      if (flags & 4) {
+        set_failed(failed, DEVERR_COPY_TIMEOUT);  // the copy did not land in time
+      } else {
+        phases ^= 1u << s;
+        if (t == 0) s_issued[s] = 0;
+      }
+    }
+    if (flags & 3) set_failed(failed, (flags & 2) ? DEVERR_LOOKBACK_TIMEOUT : 0);
+    // ---- publish this tile's count and refill the stage with the next ticket's tile ---------------
+    if (t == 0) {
+      st_relaxed_u32(&a.status[tile], failed ? ST_FAIL : (ST_DONE | tot));
+      const uint32_t nt = spare;
+      spare = atomicAdd(&a.hdr->ticket, 1u);
+      s_tk[s] = nt;
+      if (nt < T && !failed && !s_issued[s]) {
+        s_issued[s] = 1;
+        tma::fence_proxy_async_smem();
+        issue(s, nt);
+      }
+    }
+    if (failed) continue;
+    // ---- place the oldest deferred tile: the end of this CTA's tile before it plus the counts of
+    //      every tile in between (published two tiles ago or earlier) ----------------------------------
+    if (pop) {
+      const unsigned long long base = run_end + between;
+      write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+      if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
+      run_tile = pt0;
+      run_end = base + pc0;
+      pt0 = pt1;
+      pc0 = pc1;
+      ps0 = ps1;
+      --L;
+    }
+    if (tot <= (uint32_t)KCAP) {
+      // ---- defer this tile: its picks wait in the next slot -----------------------------------------
+      const int sl = (int)(pushes % KSLOTS);
+      ++pushes;
+      uint2 *dst = slots + sl * KCAP + (woff + inc - cnt);
+#pragma unroll
+      for (int j = 0; j < KWPT; ++j) {
+        if ((mask >> j) & 1u) {
+          *dst = make_uint2(mv[j], (uint32_t)(q0 + mp[j]));
+          ++dst;
+        }
+      }
+      if (L == 0) {
+        pt0 = tile;
+        pc0 = tot;
+        ps0 = sl;
+      } else {
+        pt1 = tile;
+        pc1 = tot;
+        ps1 = sl;
+      }
+      ++L;
+    } else {
+      // ---- a tile with more picks than a slot holds: place every deferred tile, then this one,
+      //      now (the threads write this tile's picks straight from their registers) -----------------
+      while (L > 0 && !failed) {
+        int b2 = 0;
+        const unsigned long long btw = cta_counts(a.status, run_tile + 1, pt0, b2, s_red_sync, s_flag_sync);
+        if (b2) {
+          set_failed(failed, (b2 & 2) ? DEVERR_LOOKBACK_TIMEOUT : 0);
+          break;
+        }
+        const unsigned long long base = run_end + btw;
+        write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+        if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
+        run_tile = pt0;
+        run_end = base + pc0;
+        pt0 = pt1;
+        pc0 = pc1;
+        ps0 = ps1;
+        --L;
+      }
+      if (!failed) {
+        int b2 = 0;
+        const unsigned long long btw = cta_counts(a.status, run_tile + 1, tile, b2, s_red_sync, s_flag_sync);
+        if (b2) {
+          set_failed(failed, (b2 & 2) ? DEVERR_LOOKBACK_TIMEOUT : 0);
+        } else {
+          const unsigned long long base = run_end + btw;
+          unsigned long long r = base + woff + inc - cnt;
+#pragma unroll
+          for (int j = 0; j < KWPT; ++j) {
+            if ((mask >> j) & 1u) {
+              if (r < a.capacity) {
+                a.key_out[r] = mv[j];
+                a.pos_out[r] = (uint32_t)(tb + q0 + mp[j]);
+              }
+              ++r;
+            }
+          }
+          if (t == 0 && tile == T - 1) a.hdr->total = base + tot;
+          run_tile = tile;
+          run_end = base + tot;
+        }
+      }
+    }
+  }
+  // ---- the deferred tiles left at the end ---------------------------------------------------------
+  while (L > 0 && !failed) {
+    int b2 = 0;
+    const unsigned long long btw = cta_counts(a.status, run_tile + 1, pt0, b2, s_red_sync, s_flag_sync);
+    if (b2) {
+      set_failed(failed, (b2 & 2) ? DEVERR_LOOKBACK_TIMEOUT : 0);
+      break;
+    }
+    const unsigned long long base = run_end + btw;
+    write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+    if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
+    run_tile = pt0;
+    run_end = base + pc0;
+    pt0 = pt1;
+    pc0 = pc1;
+    ps0 = ps1;
+    --L;
+  }
+  if (t == 0) {
+    // copies still in flight after a time-out: give them a bounded chance to land
+    if (failed)
+      for (int s = 0; s < KSTAGES; ++s)
+        if (s_issued[s]) tma::mbar_wait_bounded(&s_bar[s], (phases >> s) & 1u);
+    // the last CTA to finish publishes the count, unless some CTA failed
+    __threadfence();
+    const unsigned done = atomicAdd(&a.hdr->done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned fail = atomicAdd(&a.hdr->fail, 0u);
+      if (fail == 0) *a.count_out = *reinterpret_cast<volatile unsigned long long *>(&a.hdr->total);
+    }
+  }
+}
+
+using EncodeTiledK = PFN_cuTensorMapEncodeTiled_v12000;
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no -lcuda).
+EncodeTiledK encode_tiled_k() {
+  static EncodeTiledK fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledK>(p);
+  });
+  return fn;
+}
+
+template <int W>
+cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms, cudaStream_t st) {
+  auto kern = k_keys_min<W>;
+  static int per_sm[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
+  if (nb == 0) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KSMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, KNT, KSMEM);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    if (dev >= 0 && dev < 64) per_sm[dev] = nb;
+  }
+  uint64_t grid = (uint64_t)num_sms * (uint64_t)nb;
+  if (grid > a.num_tiles) grid = a.num_tiles;
+  kern<<<(unsigned)grid, KNT, KSMEM, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool keys_min_applies(const uint32_t *keys, uint64_t m, int w) {
+  return w >= 1 && w <= KMAXW && m >= 32 && m < (1ull << 32) && (uint64_t)w <= m &&
+         (reinterpret_cast<uintptr_t>(keys) & 15u) == 0 && encode_tiled_k() != nullptr;
+}
+
+uint64_t keys_min_ws_bytes(uint64_t m, int w) {
+  const uint64_t nwin = m - (uint64_t)w + 1;
+  return 256 + (nwin + KTILE - 1) / KTILE * 4;
+}
+
+cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *key_out, uint32_t *pos_out,
+                            uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
+                            cudaStream_t st) {
+  if (!keys_min_applies(keys, m, w)) return cudaErrorInvalidValue;
+  const uint64_t nwin = m - (uint64_t)w + 1;
+  const uint64_t tiles = (nwin + KTILE - 1) / KTILE;
+  const uint64_t rows = m / 32;
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {32, rows};
+  const cuuint64_t gstride[1] = {128};
+  const cuuint32_t box[2] = {32, (cuuint32_t)KROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode_tiled_k()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(keys), gdim, gstride, box,
+                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(ws, 0, keys_min_ws_bytes(m, w), st);
+  if (e != cudaSuccess) return e;
+  KeysArgs a{};
+  a.keys = keys;
+  a.m = m;
+  a.n_full = rows * 32;
+  a.nwin = nwin;
+  a.num_tiles = (uint32_t)tiles;
+  a.hdr = static_cast<KeysHeader *>(ws);
+  a.status = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
+  a.key_out = key_out;
+  a.pos_out = pos_out;
+  a.capacity = capacity;
+  a.count_out = count_out;
+  a.err = err;
+  a.vec_ok = ((reinterpret_cast<uintptr_t>(key_out) - reinterpret_cast<uintptr_t>(pos_out)) & 15u) == 0 &&
+             (reinterpret_cast<uintptr_t>(key_out) & 3u) == 0;
+  switch (w) {
+    case 1: return launch_w_keys<1>(map, a, num_sms, st);
+    case 2: return launch_w_keys<2>(map, a, num_sms, st);
+    case 3: return launch_w_keys<3>(map, a, num_sms, st);
+    case 4: return launch_w_keys<4>(map, a, num_sms, st);
+    case 5: return launch_w_keys<5>(map, a, num_sms, st);
+    case 6: return launch_w_keys<6>(map, a, num_sms, st);
+    case 7: return launch_w_keys<7>(map, a, num_sms, st);
+    case 8: return launch_w_keys<8>(map, a, num_sms, st);
+    case 9: return launch_w_keys<9>(map, a, num_sms, st);
+    case 10: return launch_w_keys<10>(map, a, num_sms, st);
+    case 11: return launch_w_keys<11>(map, a, num_sms, st);
+    case 12: return launch_w_keys<12>(map, a, num_sms, st);
+    case 13: return launch_w_keys<13>(map, a, num_sms, st);
+    case 14: return launch_w_keys<14>(map, a, num_sms, st);
+    case 15: return launch_w_keys<15>(map, a, num_sms, st);
+    case 16: return launch_w_keys<16>(map, a, num_sms, st);
+    case 17: return launch_w_keys<17>(map, a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sws

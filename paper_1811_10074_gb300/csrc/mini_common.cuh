@@ -18,8 +18,6 @@ constexpr unsigned long long FLAG_AGG = 1ull << 62;
 constexpr unsigned long long FLAG_INC = 2ull << 62;
 constexpr unsigned long long FLAG_ERR = 3ull << 62;
 constexpr unsigned long long VALUE_MASK = (1ull << 62) - 1;
-constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;  // x >= 64 ns sleep: about a second at most
-constexpr int COPY_SPIN_LIMIT = 1 << 22;
 
 // ---- PTX helpers ----------------------------------------------------------------------------
 using tma::bulk_g2s;
@@ -71,18 +69,11 @@ __device__ inline bool stage_bytes(uint8_t *sdst, const uint8_t *__restrict__ se
   __syncthreads();
   bool ok = true;
   if (bulk > 0) {
-    int spins = 0;
-    while (!mbar_try_wait(bar, 0)) {
-      if (++spins > COPY_SPIN_LIMIT) {
-        ok = false;
-        break;
-      }
-      __nanosleep(32);
-    }
+    ok = tma::mbar_wait_bounded(bar, 0);
     if (!ok) {
       atomicOr(err, DEVERR_COPY_TIMEOUT);
-      // give the copy one more bounded chance to land before the CTA can exit
-      for (int s = 0; s < COPY_SPIN_LIMIT && !mbar_try_wait(bar, 0); ++s) __nanosleep(64);
+      // give an issued copy one more bounded chance to land before the CTA can exit
+      if (issue) tma::mbar_wait_bounded(bar, 0);
     }
   }
   return ok;
@@ -217,11 +208,13 @@ __device__ inline unsigned long long lookback_warp(unsigned long long *status, u
   while (true) {
     const long long idx = base - lane;
     unsigned long long s = FLAG_INC;
-    int spins = 0;
+    unsigned long long t0 = 0;
     while (true) {
       s = idx >= 0 ? ld_relaxed(&status[idx]) : FLAG_INC;
       if (__all_sync(kFull, (s >> 62) != 0ull)) break;
-      if (++spins > LOOKBACK_SPIN_LIMIT) {
+      const unsigned long long now = tma::now_ns();
+      if (t0 == 0) t0 = now;
+      if (now - t0 > tma::kWaitNs) {
         failed = true;
         break;
       }
@@ -243,66 +236,6 @@ __device__ inline unsigned long long lookback_warp(unsigned long long *status, u
     base -= 32;
   }
   if (lane == 0) {
-    if (failed) {
-      st_relaxed(&status[tile], FLAG_ERR);
-      atomicOr(err, DEVERR_LOOKBACK_TIMEOUT);
-    } else {
-      st_relaxed(&status[tile], FLAG_INC | (excl + agg));
-    }
-  }
-  return excl;
-}
-
-// CTA-wide look-back: every thread polls one predecessor, so each round trip to L2 inspects
-// blockDim.x tiles and the frontier of known inclusive prefixes advances that many tiles per
-// round trip (a warp-wide look-back advances it by only 32).  All threads of the CTA must call
-// it; `red` is shared scratch of at least 2 * (blockDim.x / 32) + 2 words.  Returns the number of
-// picks of all earlier tiles; sets `failed` when a bounded wait ran out or an earlier tile failed.
-__device__ inline unsigned long long lookback_cta(unsigned long long *status, uint32_t tile,
-                                                  unsigned long long agg, int *err, bool &failed,
-                                                  unsigned long long *red) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  failed = false;
-  if (tile == 0) {
-    if (t == 0) st_relaxed(&status[0], FLAG_INC | agg);
-    return 0;
-  }
-  if (t == 0) st_relaxed(&status[tile], FLAG_AGG | agg);
-  unsigned long long excl = 0;
-  long long base = (long long)tile - 1;
-  while (true) {
-    const long long idx = base - t;
-    unsigned long long s = idx >= 0 ? ld_relaxed(&status[idx]) : FLAG_INC;
-    int spins = 0;
-    while (!__syncthreads_and((s >> 62) != 0ull)) {
-      if (++spins > LOOKBACK_SPIN_LIMIT) {
-        failed = true;
-        break;
-      }
-      __nanosleep(64);
-      if ((s >> 62) == 0ull) s = ld_relaxed(&status[idx]);
-    }
-    if (failed) break;
-    if (__syncthreads_or((s >> 62) == 3ull)) {
-      failed = true;
-      break;
-    }
-    // the nearest predecessor holding an inclusive prefix
-    const unsigned inc = __ballot_sync(kFull, (s >> 62) == 2ull);
-    if (lane == 0) red[warp] = inc ? (unsigned long long)(warp * 32 + __ffs(inc) - 1) : ~0ull;
-    __syncthreads();
-    unsigned long long first = ~0ull;
-    for (int i = 0; i < nw; ++i) first = red[i] < first ? red[i] : first;
-    unsigned long long v = (first == ~0ull || (unsigned long long)t <= first) ? (s & VALUE_MASK) : 0ull;
-    v = warp_sum_u64(v);
-    if (lane == 0) red[nw + warp] = v;
-    __syncthreads();
-    for (int i = 0; i < nw; ++i) excl += red[nw + i];
-    __syncthreads();
-    if (first != ~0ull) break;
-    base -= blockDim.x;
-  }
-  if (t == 0) {
     if (failed) {
       st_relaxed(&status[tile], FLAG_ERR);
       atomicOr(err, DEVERR_LOOKBACK_TIMEOUT);

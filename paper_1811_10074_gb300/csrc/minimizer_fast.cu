@@ -155,17 +155,10 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
     bool ok = true;
     if (stg.bulk > 0) {
       const uint32_t ph = (phases >> b) & 1u;
-      int spins = 0;
-      while (!mbar_try_wait(&s_mbar[b], ph)) {
-        if (++spins > COPY_SPIN_LIMIT) {
-          ok = false;
-          break;
-        }
-        __nanosleep(32);
-      }
+      ok = tma::mbar_wait_bounded(&s_mbar[b], ph);
       if (!ok) {
         if (t == 0) atomicOr(a.err, DEVERR_COPY_TIMEOUT);
-        for (int s = 0; s < COPY_SPIN_LIMIT && !mbar_try_wait(&s_mbar[b], ph); ++s) __nanosleep(64);
+        tma::mbar_wait_bounded(&s_mbar[b], ph);  // one more bounded chance for the copy to land
       }
       phases ^= 1u << b;
     }

@@ -23,7 +23,7 @@ __global__ void k_selftest_wait(int which, unsigned long long *status, int *err)
     tma::mbar_init(&bar, 1);
     tma::fence_mbar_init();
     tma::mbar_arrive_expect_tx(&bar, 16u);
-    if (!tma::mbar_wait_bounded(&bar, 0u, mini::COPY_SPIN_LIMIT)) atomicOr(err, DEVERR_COPY_TIMEOUT);
+    if (!tma::mbar_wait_bounded(&bar, 0u)) atomicOr(err, DEVERR_COPY_TIMEOUT);
   }
 }
 

@@ -215,10 +215,9 @@ __global__ void __launch_bounds__(NT) k_slide_al(const typename Op::T *__restric
 // with zeros); the threads that own them load them directly.  Every wait is bounded; on a
 // time-out the CTA flags DEVERR_COPY_TIMEOUT, lets its own copies land (bounded) and returns.
 constexpr int kStreamRowBytes = 128;
-constexpr int kStreamSpinLimit = 1 << 22;
 
 __device__ __forceinline__ bool stream_wait(unsigned long long *bar, uint32_t parity) {
-  return tma::mbar_wait_bounded(bar, parity, kStreamSpinLimit);
+  return tma::mbar_wait_bounded(bar, parity);
 }
 
 template <class Op, int NT, int VPT, int STAGES, int MINB>

@@ -54,13 +54,24 @@ __device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map,
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// Wait for the phase of `bar` with the given parity: spin briefly, then poll with a short sleep,
-// and give up after `limit` polls (about a second at 2^22).  Returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, int limit) {
-  for (int spins = 0; !mbar_try_wait(bar, parity);) {
-    if (++spins > limit) return false;
-    if (spins > 64) __nanosleep(64);
-  }
+// Device time in nanoseconds (the global timer).
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Every bounded wait of the library gives up after this long (measured on the global timer, so
+// the bound holds however long one poll takes).
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+// Wait for the phase of `bar` with the given parity (try_wait suspends the thread between
+// polls), giving up after limit_ns.  Returns false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (now_ns() - t0 > limit_ns) return false;
   return true;
 }
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
