@@ -56,7 +56,8 @@ constexpr int KSTAGE_STRIDE = (KSTAGE_BYTES + 1023) / 1024 * 1024;  // 1024-alig
 constexpr int KSTAGES = 3;
 constexpr int KSLOTS = 3;                 // pick slots: a tile is placed two tiles after it is counted
 constexpr int KCAP = 2560;                // picks a slot holds (more: the tile is placed at once)
-constexpr size_t KSMEM = 1024 + (size_t)KSTAGES * KSTAGE_STRIDE + (size_t)KSLOTS * KCAP * 8;
+constexpr int KSLOT_BYTES = KCAP * 8;     // (key, tile-relative position) per pick
+constexpr size_t KSMEM = 1024 + (size_t)KSTAGES * KSTAGE_STRIDE + (size_t)KSLOTS * KSLOT_BYTES;  // 2 CTAs/SM
 constexpr uint32_t ST_DONE = 0x80000000u;  // status: count published (low bits)
 constexpr uint32_t ST_FAIL = 0xC0000000u;  // status: the tile failed
 constexpr uint32_t ST_COUNT = 0x3FFFFFFFu;
@@ -72,9 +73,9 @@ struct KeysHeader {
 
 struct KeysArgs {
   const uint32_t *keys;
-  uint64_t m;          // keys
-  uint64_t n_full;     // keys in whole 32-key rows (the tensor map's extent)
-  uint64_t nwin;       // windows = m - w + 1
+  uint32_t m;          // keys (at most 2^32 - 2^14, so that every index below fits 32 bits)
+  uint32_t n_full;     // keys in whole 32-key rows (the tensor map's extent)
+  uint32_t nwin;       // windows = m - w + 1
   uint32_t num_tiles;
   uint32_t *status;    // one word per tile, zeroed before the launch
   KeysHeader *hdr;     // zeroed before the launch
@@ -83,7 +84,6 @@ struct KeysArgs {
   uint64_t capacity;
   uint64_t *count_out;
   int *err;
-  int vec_ok;  // key_out and pos_out are 16-byte aligned at the same phase (vector stores)
 };
 
 __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
@@ -168,20 +168,6 @@ __device__ __forceinline__ void window_minima(const uint32_t (&X)[32], uint32_t 
   }
 }
 
-// Thread-relative position of the pick of the window just before the thread's first (keys
-// xm1 = X[-1], X[0 .. W-2]).
-template <int W>
-__device__ __forceinline__ int prev_window_pick(uint32_t xm1, const uint32_t (&X)[32]) {
-  uint32_t v = xm1;
-  int p = -1;
-#pragma unroll
-  for (int i = 0; i < W - 1; ++i)
-    if (X[i] < v) {
-      v = X[i];
-      p = i;
-    }
-  return p;
-}
 
 
 // This thread's share of the counts of tiles lo .. hi-1, polling (bounded) any not yet published.
@@ -252,42 +238,26 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
   return sum;
 }
 
-// Copy a placed tile's picks from its slot to the output (keys, positions), coalesced: after up to
-// three single picks that reach a 16-byte boundary of the output, four picks per thread and
-// store (two 16-byte stores), then the tail.  When the picks run past the capacity, or the two
-// output arrays are not both 16-byte aligned at the same phase, one pick per thread and store.
-__device__ __forceinline__ void write_slot(const uint2 *slot, uint32_t cnt, uint32_t tile, unsigned long long base,
-                                           const KeysArgs &a) {
+// Copy a placed tile's picks from its slot to the output (keys, positions): one pick per thread
+// and round, so every warp store covers 128 consecutive bytes.
+__device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t cnt, uint32_t tile,
+                                           unsigned long long base, const KeysArgs &a) {
+  const uint2 *sl = reinterpret_cast<const uint2 *>(slot);
   const uint32_t pos0 = tile * (uint32_t)KTILE;
-  if (a.vec_ok && base + cnt <= a.capacity) {
+  if (base + cnt <= a.capacity) {
     uint32_t *ko = a.key_out + base;
     uint32_t *po = a.pos_out + base;
-    const uint32_t head = (uint32_t)(((16u - (reinterpret_cast<uintptr_t>(ko) & 15u)) & 15u) >> 2);
-    const uint32_t h = head < cnt ? head : cnt;
-    const uint32_t nq = (cnt - h) >> 2;
-    if (threadIdx.x < h) {
-      const uint2 pk = slot[threadIdx.x];
-      ko[threadIdx.x] = pk.x;
-      po[threadIdx.x] = pos0 + pk.y;
-    }
-    for (uint32_t q = threadIdx.x; q < nq; q += KNT) {
-      const uint32_t x = h + 4 * q;
-      const uint2 p0 = slot[x], p1 = slot[x + 1], p2 = slot[x + 2], p3 = slot[x + 3];  // 8-byte aligned
-      *reinterpret_cast<uint4 *>(ko + x) = make_uint4(p0.x, p1.x, p2.x, p3.x);
-      *reinterpret_cast<uint4 *>(po + x) = make_uint4(pos0 + p0.y, pos0 + p1.y, pos0 + p2.y, pos0 + p3.y);
-    }
-    const uint32_t x = h + 4 * nq + threadIdx.x;
-    if (x < cnt) {
-      const uint2 pk = slot[x];
+    for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
+      const uint2 pk = sl[x];
       ko[x] = pk.x;
       po[x] = pos0 + pk.y;
     }
     return;
   }
   for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
-    const uint2 pk = slot[x];
     const unsigned long long gi = base + x;
     if (gi < a.capacity) {
+      const uint2 pk = sl[x];
       a.key_out[gi] = pk.x;
       a.pos_out[gi] = pos0 + pk.y;
     }
@@ -306,7 +276,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   __shared__ unsigned long long s_red_sync[KNT / 32];
   __shared__ int s_flag_sync[KNT / 32];
   unsigned char *stages = ksm_raw + ((1024u - (tma::smem_u32(ksm_raw) & 1023u)) & 1023u);
-  uint2 *slots = reinterpret_cast<uint2 *>(stages + KSTAGES * KSTAGE_STRIDE);
+  unsigned char *slots = stages + KSTAGES * KSTAGE_STRIDE;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t T = a.num_tiles;
   constexpr uint32_t NONE = 0xFFFFFFFFu;
@@ -341,7 +311,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   __syncthreads();
 
   uint32_t phases = 0;             // bit s: parity of stage s's next completion
-  long long run_tile = -1;         // the last tile whose picks were placed ...
+  int run_tile = -1;               // the last tile whose picks were placed ...
   unsigned long long run_end = 0;  // ... and the end of its picks in the output
   // tiles counted but not yet placed (at most KSLOTS - 1), oldest first, with their slots
   int L = 0;
@@ -365,14 +335,14 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     // the counts before the oldest deferred tile (placed after this tile's barrier): two status
     // words per thread read now, so that the round trip overlaps this tile's work
     const bool pop = L == KSLOTS - 1 && !failed;
-    const long long j0 = run_tile + 1 + t;
+    const int j0 = run_tile + 1 + t;
     uint32_t sv0 = 0, sv1 = 0;
-    if (pop && j0 < (long long)pt0) sv0 = ld_relaxed_u32(&a.status[j0]);
-    if (pop && j0 + KNT < (long long)pt0) sv1 = ld_relaxed_u32(&a.status[j0 + KNT]);
+    if (pop && j0 < (int)pt0) sv0 = ld_relaxed_u32(&a.status[j0]);
+    if (pop && j0 + KNT < (int)pt0) sv1 = ld_relaxed_u32(&a.status[j0 + KNT]);
     const bool ok = issued && tma::mbar_wait_bounded(&s_bar[s], (phases >> s) & 1u);
     const bool wok = __all_sync(kFull, ok);
-    const uint64_t tb = (uint64_t)tile * KTILE;  // first window (and key) of the tile
-    const uint64_t g0 = tb + (uint64_t)q0;      // this thread's first window
+    const uint32_t tb = tile * (uint32_t)KTILE;  // first window (and key) of the tile
+    const uint32_t g0 = tb + (uint32_t)q0;      // this thread's first window
     uint32_t mv[KWPT];
     int mp[KWPT];
     unsigned mask = 0;  // windows that store a pick
@@ -404,7 +374,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       if (g0 + KWPT + W - 1 > a.n_full) {  // keys of the final partial row (or past the end)
 #pragma unroll
         for (int i = 0; i < KWPT + W - 1; ++i) {
-          const uint64_t gi = g0 + (uint64_t)i;
+          const uint32_t gi = g0 + (uint32_t)i;
           if (gi >= a.n_full) X[i] = gi < a.m ? a.keys[gi] : 0xFFFFFFFFu;
         }
         if (lane == 0 && g0 >= 1 && g0 - 1 >= a.n_full && g0 - 1 < a.m) xm1 = a.keys[g0 - 1];
@@ -412,16 +382,24 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       window_minima<W>(X, mv, mp);
       // the pick of the window before this thread's first: the previous lane's last, shifted to
       // this thread's frame; lane 0 of each warp finds it from its own keys
-      int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
-      if (lane == 0) pp = g0 == 0 ? -1000 : prev_window_pick<W>(xm1, X);
-      // windows that store a pick: a pick other than the window before's, inside the sequence
+      // A window stores a pick when its pick differs from the previous window's pick: when its
+      // least key differs from the previous window's, or equals it but the previous window's pick
+      // was its first key (which has left).  Values decide it; the window before this thread's
+      // first is the previous lane's last (lane 0 of each warp computes it).
+      uint32_t pm = __shfl_up_sync(kFull, mv[KWPT - 1], 1);
+      uint32_t px = __shfl_up_sync(kFull, X[KWPT - 1], 1);
+      if (lane == 0) {
+        pm = xm1;
 #pragma unroll
-      for (int j = 0; j < KWPT; ++j) {
-        mask |= (unsigned)(mp[j] != pp) << j;
-        pp = mp[j];
+        for (int i = 0; i < W - 1; ++i) pm = min(pm, X[i]);
+        px = xm1;
       }
-      const long long left = (long long)a.nwin - (long long)g0;
-      if (left < KWPT) mask &= left <= 0 ? 0u : ((1u << left) - 1u);
+      mask = (mv[0] != pm || px == pm || g0 == 0) ? 1u : 0u;
+#pragma unroll
+      for (int j = 1; j < KWPT; ++j) mask |= (unsigned)(mv[j] != mv[j - 1] || X[j - 1] == mv[j - 1]) << j;
+      const int left = (int)(a.nwin - g0);  // windows of this thread inside the sequence (if > 0)
+      if (g0 >= a.nwin) mask = 0;
+      else if (left < KWPT) mask &= (1u << left) - 1u;
     }
     const uint32_t cnt = __popc(mask);
     uint32_t inc = cnt;
@@ -434,9 +412,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     int bad = 0;
     uint32_t part = 0;
     if (pop) {
-      if (j0 < (long long)pt0) part += await_status(&a.status[j0], sv0, bad) & ST_COUNT;
-      if (j0 + KNT < (long long)pt0) part += await_status(&a.status[j0 + KNT], sv1, bad) & ST_COUNT;
-      if (run_tile + 1 + 2 * KNT < (long long)pt0)  // a long gap (rare): the rest
+      if (j0 < (int)pt0) part += await_status(&a.status[j0], sv0, bad) & ST_COUNT;
+      if (j0 + KNT < (int)pt0) part += await_status(&a.status[j0 + KNT], sv1, bad) & ST_COUNT;
+      if (run_tile + 1 + 2 * KNT < (int)pt0)  // a long gap (rare): the rest
         part += (uint32_t)partial_counts(a.status, run_tile + 1 + 2 * KNT, pt0, bad);
     }
     part = __reduce_add_sync(kFull, part);
@@ -481,7 +459,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     //      every tile in between (published two tiles ago or earlier) ----------------------------------
     if (pop) {
       const unsigned long long base = run_end + between;
-      write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+      write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
       if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
       run_tile = pt0;
       run_end = base + pc0;
@@ -494,7 +472,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       // ---- defer this tile: its picks wait in the next slot -----------------------------------------
       const int sl = (int)(pushes % KSLOTS);
       ++pushes;
-      uint2 *dst = slots + sl * KCAP + (woff + inc - cnt);
+      uint2 *dst = reinterpret_cast<uint2 *>(slots + sl * KSLOT_BYTES) + (woff + inc - cnt);
 #pragma unroll
       for (int j = 0; j < KWPT; ++j) {
         if ((mask >> j) & 1u) {
@@ -523,7 +501,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           break;
         }
         const unsigned long long base = run_end + btw;
-        write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+        write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
         if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
         run_tile = pt0;
         run_end = base + pc0;
@@ -545,7 +523,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
             if ((mask >> j) & 1u) {
               if (r < a.capacity) {
                 a.key_out[r] = mv[j];
-                a.pos_out[r] = (uint32_t)(tb + q0 + mp[j]);
+                a.pos_out[r] = tb + (uint32_t)(q0 + mp[j]);
               }
               ++r;
             }
@@ -566,7 +544,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       break;
     }
     const unsigned long long base = run_end + btw;
-    write_slot(slots + ps0 * KCAP, pc0, pt0, base, a);
+    write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
     if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
     run_tile = pt0;
     run_end = base + pc0;
@@ -632,7 +610,7 @@ cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms
 }  // namespace
 
 bool keys_min_applies(const uint32_t *keys, uint64_t m, int w) {
-  return w >= 1 && w <= KMAXW && m >= 32 && m < (1ull << 32) && (uint64_t)w <= m &&
+  return w >= 1 && w <= KMAXW && m >= 32 && m <= (1ull << 32) - (1ull << 14) && (uint64_t)w <= m &&
          (reinterpret_cast<uintptr_t>(keys) & 15u) == 0 && encode_tiled_k() != nullptr;
 }
 
@@ -661,9 +639,9 @@ cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *k
   if (e != cudaSuccess) return e;
   KeysArgs a{};
   a.keys = keys;
-  a.m = m;
-  a.n_full = rows * 32;
-  a.nwin = nwin;
+  a.m = (uint32_t)m;
+  a.n_full = (uint32_t)(rows * 32);
+  a.nwin = (uint32_t)nwin;
   a.num_tiles = (uint32_t)tiles;
   a.hdr = static_cast<KeysHeader *>(ws);
   a.status = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
@@ -672,8 +650,6 @@ cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *k
   a.capacity = capacity;
   a.count_out = count_out;
   a.err = err;
-  a.vec_ok = ((reinterpret_cast<uintptr_t>(key_out) - reinterpret_cast<uintptr_t>(pos_out)) & 15u) == 0 &&
-             (reinterpret_cast<uintptr_t>(key_out) & 3u) == 0;
   switch (w) {
     case 1: return launch_w_keys<1>(map, a, num_sms, st);
     case 2: return launch_w_keys<2>(map, a, num_sms, st);
