@@ -18,16 +18,20 @@
 // registers.  Keys compare by value and carry their position (a compile-time constant): a suffix
 // step takes an equal key (the left one), a prefix step does not, and the suffix part wins ties
 // against the prefix part, so every window knows its leftmost least key.  A window stores a pick
-// when its pick's position differs from the previous window's.
+// when its pick differs from the previous window's pick, which the values decide: its least key
+// differs from the previous window's, or equals it while the previous pick was the previous
+// window's first key (which has left).
 //
 // Order.  Tiles are handed out by an atomic ticket, in order, and each CTA takes its tickets in
 // increasing order.  A tile's pick count goes to its status word as soon as it is known; the
-// tile's picks wait in shared memory while the CTA computes its next tile, and then the CTA finds
-// their output offset as the end of its own previous tile's picks plus the counts of all tiles
-// between the two -- published by now, since each is published right after it is computed and
-// every ticket below this one is held by a running CTA.  That costs each thread one or two reads
-// of hot status words per tile; there is no staging area, no second pass, no inclusive-prefix
-// chain.  Every wait is bounded: a wait that runs out records the fault, the CTA publishes a
+// tile's picks wait in one of three shared-memory slots while the CTA computes its next two
+// tiles, and then the CTA finds their output offset as the end of its own previous tile's picks
+// plus the counts of all tiles between the two -- published by then, since each is published
+// right after it is computed and every ticket below this one is held by a running CTA (the two
+// tiles of slack absorb CTAs that run behind).  That costs each thread one or two reads of hot
+// status words per tile, issued before the tile's work; there is no staging area, no second
+// pass, no inclusive-prefix chain, and one CTA barrier per tile.  A tile with more picks than a
+// slot holds is placed at once, after the deferred ones.  Every wait is bounded: a wait that runs out records the fault, the CTA publishes a
 // failure mark instead of its later counts, and every tile after it then fails as well (its
 // offset would include a missing count), so the final count is never written.
 #include <cstdint>
