@@ -685,12 +685,15 @@ def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain
             "speedup_batched_vs_plain": round(batched["gbp_s"] / max(plain_r["gbp_s"], 1e-9), 1)}
 
 
-def serve_extras(ctx, n_requests: int = 1500, loads=(0.5, 1.0, 1.5, 2.0), duration_s: float = 1.5):
-    """Serving: requests of log-uniform length in [150 bp, 1 Mbp] (k=15, w=10).  Capacity is the
-    throughput of a burst of all requests handed over in one call (the server's drain rate);
-    then Poisson arrivals at fractions of it, each due request submitted as soon as its arrival
-    time has passed (those due together in one call); p50/p99 of submit-to-answer latency, the
-    client's submission lateness, and the bases per second answered."""
+def serve_extras(ctx, n_requests: int = 3000, loads=(0.5, 1.0, 1.5, 2.0), duration_s: float = 1.5):
+    """Serving: requests of log-uniform length in [150 bp, 1 Mbp] (k=15, w=10).  A drainer thread
+    collects answers as they come (sws_server_collect: many per call, read in place in the
+    server's pinned memory) and releases them.  Capacity is the sustained drain rate of a burst of
+    all requests handed over in one call, measured at the client (first submission to last
+    answer collected).  Then Poisson arrivals at fractions of it, each due request submitted as
+    soon as its arrival time has passed (those due together in one call): p50/p99 latency
+    (submission to answer on the host), the client's submission lateness and the bases per second
+    answered."""
     import paper_1811_10074_gb300 as P
     from paper_1811_10074_gb300 import synth
     lens = synth.loguniform_lengths(n_requests, 150, 1_000_000, seed=42)
@@ -700,49 +703,61 @@ def serve_extras(ctx, n_requests: int = 1500, loads=(0.5, 1.0, 1.5, 2.0), durati
     reqs = [(pool[starts[i] // 4: (starts[i] + lens[i] + 3) // 4], int(lens[i])) for i in range(n_requests)]
     srv = P.Server(15, 10, slots=4, max_requests_per_batch=128, max_bases_per_batch=1 << 24, ctx=ctx)
 
-    def drain(ids):
-        for rid in ids:
-            srv.wait(rid, 120.0)
-            srv.result(rid)
-
     def run(arrivals):
+        """Submit reqs[i % n] at arrivals[i]; return (server stats, bases, lateness, client span)."""
         srv.reset_stats()
-        ids, late, bases = [], [], 0
-        nxt = 0
+        total = len(arrivals)
+        state = {"got": 0, "t_last": 0.0}
+
+        def drainer():
+            while state["got"] < total:
+                ids = srv.collect_raw(4096, 0.05)[0]
+                if ids.size:
+                    srv.release(ids)
+                    state["got"] += ids.size
+                    state["t_last"] = time.perf_counter()
+
+        th = threading.Thread(target=drainer)
+        th.start()
+        late, bases, nxt = [], 0, 0
         t0 = time.perf_counter()
-        while nxt < len(arrivals):
+        while nxt < total:
             now = time.perf_counter() - t0
             if arrivals[nxt] > now:
                 time.sleep(min(arrivals[nxt] - now, 0.001))
                 continue
             due = nxt
-            while due < len(arrivals) and arrivals[due] <= now:
+            while due < total and arrivals[due] <= now:
                 due += 1
             batch = [reqs[i % n_requests] for i in range(nxt, due)]
-            ids += srv.submit_many(batch)
+            srv.submit_many(batch)
             t_sub = time.perf_counter() - t0
             late += [t_sub - arrivals[i] for i in range(nxt, due)]
             bases += sum(L for _, L in batch)
             nxt = due
-        drain(ids)
-        return srv.stats(), bases, np.array(late)
+        th.join()
+        return srv.stats(), bases, np.array(late), state["t_last"] - t0
 
     run([0.0] * 64)  # warm up
-    st, bases, _ = run([0.0] * n_requests)
-    cap_bps = bases / st["span_s"]
+    st, bases, _, span = run([0.0] * n_requests)
+    cap_bps = bases / span
     mean_len = float(np.mean(lens))
     out = {"workload": "requests log-uniform 150 bp - 1 Mbp, uniform ACGT, k=15 w=10; 4 slots, <=128 requests "
-                       "and <=16 Mbp per batch",
+                       "and <=16 Mbp per batch; answers collected in place and released by a client thread",
            "capacity_gbp_s": round(cap_bps / 1e9, 3), "burst_requests": n_requests,
-           "burst_p50_ms": round(st["p50_s"] * 1e3, 3), "burst_p99_ms": round(st["p99_s"] * 1e3, 3), "loads": []}
+           "capacity_definition": "sustained drain rate: a burst of all requests, first submission to last "
+                                  "answer collected by the client",
+           "server_side_gbp_s": round(st["bases"] / max(st["span_s"], 1e-9) / 1e9, 3),
+           "burst_p50_ms": round(st["p50_s"] * 1e3, 3), "burst_p99_ms": round(st["p99_s"] * 1e3, 3),
+           "batches": int(st["batches"]), "loads": []}
     for f in loads:
         rate = f * cap_bps / mean_len
         count = max(64, int(rate * duration_s))
         arrivals = list(synth.poisson_arrivals(count, rate, seed=int(100 * f)))
-        st, bases, late = run(arrivals)
+        st, bases, late, span = run(arrivals)
         out["loads"].append({"offered_x_capacity": f, "requests": count, "arrival_rate_per_s": round(rate, 1),
                              "p50_ms": round(st["p50_s"] * 1e3, 3), "p99_ms": round(st["p99_s"] * 1e3, 3),
-                             "max_ms": round(st["max_s"] * 1e3, 3), "gbp_s": round(bases / st["span_s"] / 1e9, 3),
+                             "max_ms": round(st["max_s"] * 1e3, 3), "gbp_s": round(bases / span / 1e9, 3),
                              "batches": int(st["batches"]),
                              "client_late_p99_ms": round(float(np.percentile(late, 99)) * 1e3, 3)})
     srv.close()

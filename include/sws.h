@@ -264,7 +264,9 @@ sws_status sws_batch_sync(sws_batch *b);
  * as soon as a slot is free.  A request is admitted while the device bytes it needs fit
  * hbm_budget_bytes next to those in flight.  Results are those of sws_minimizers on the request
  * alone (uint32 keys, so k <= 16; positions from 0).  Latency is measured from submission to the
- * moment the worker sees the result on the host. */
+ * moment the worker sees the result on the host.  Submitted bases are copied once, into pinned
+ * memory; answers stay in pinned memory until released (sws_server_collect / _release) or copied
+ * out (sws_server_result). */
 typedef struct sws_server sws_server;
 typedef struct sws_server_config {
   int k, w, mode;                  /* as for sws_minimizers (k <= 16)                          */
@@ -290,12 +292,26 @@ sws_status sws_server_submit_batch(sws_server *s, const uint8_t *const *packed, 
                                    uint64_t *request_ids);
 /* Wait up to timeout_s seconds (0: just look) for a request; *done = 1 once it is answered. */
 sws_status sws_server_wait(sws_server *s, uint64_t request_id, double timeout_s, int *done);
-/* Copy an answered request's picks to host buffers and forget the request. */
+/* Copy an answered request's picks to host buffers and forget the request (whether or not it was
+ * collected).  SWS_ERR_CAPACITY (with *count set) if capacity is too small; the request stays. */
 sws_status sws_server_result(sws_server *s, uint64_t request_id, uint32_t *hash, uint32_t *pos, uint64_t capacity,
                              uint64_t *count, double *latency_s);
+/* Collect up to max_n answered requests not collected before, in the order they were answered,
+ * waiting up to timeout_s seconds (0: just look) for the first.  For each: its id, pick count,
+ * pointers to its keys and positions IN THE SERVER'S PINNED RESULT MEMORY (read them in place; no
+ * copy is made), and its latency (latency_s may be NULL).  *n_out = the number collected.  The
+ * pointers stay valid until the request is released; a server holds 2 * slots + 2 result blocks
+ * (one per batch), and a batch whose block is still held by unreleased answers waits, so release
+ * promptly. */
+sws_status sws_server_collect(sws_server *s, uint64_t max_n, double timeout_s, uint64_t *ids, uint64_t *counts,
+                              const uint32_t **hash, const uint32_t **pos, double *latency_s, uint64_t *n_out);
+/* Forget n answered requests (collected or not) and give their result memory back.  An id that is
+ * unknown or not yet answered: SWS_ERR_INVALID (the others are still released). */
+sws_status sws_server_release(sws_server *s, const uint64_t *ids, uint64_t n);
 sws_status sws_server_stats(sws_server *s, sws_server_statistics *out);
 sws_status sws_server_reset_stats(sws_server *s);
-/* Finish queued and running requests, stop the worker and free everything. */
+/* Finish running and queued requests (queued ones only while a result block is free for them),
+ * stop the worker and free everything, answers not yet released included. */
 sws_status sws_server_destroy(sws_server *s);
 
 /* ---- minimizers without allocation ------------------------------------------------------ */

@@ -71,6 +71,8 @@ SIGNATURES = {
     "sws_server_submit_batch": (i32, [vp, vp, vp, u64, vp]),
     "sws_server_wait": (i32, [vp, u64, ctypes.c_double, ctypes.POINTER(i32)]),
     "sws_server_result": (i32, [vp, u64, vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]),
+    "sws_server_collect": (i32, [vp, u64, ctypes.c_double, vp, vp, vp, vp, vp, ctypes.POINTER(u64)]),
+    "sws_server_release": (i32, [vp, vp, u64]),
     "sws_server_stats": (i32, [vp, vp]),
     "sws_server_reset_stats": (i32, [vp]),
     "sws_server_destroy": (i32, [vp]),
@@ -502,6 +504,39 @@ class Server:
             _check(st)
             c = int(cnt.value)
             return h[:c], p[:c], float(lat.value)
+
+    def collect_raw(self, max_n: int = 4096, timeout: float = 0.0):
+        """Collect up to max_n answered requests: numpy arrays (ids, counts, latencies seconds,
+        key pointers, position pointers).  The answers stay in the server's pinned memory until
+        :meth:`release`; :meth:`views` turns one pair of pointers into arrays."""
+        import numpy as np
+        ids = np.empty(max(max_n, 1), dtype=np.uint64)
+        cnt = np.empty(max(max_n, 1), dtype=np.uint64)
+        lat = np.empty(max(max_n, 1), dtype=np.float64)
+        hp = np.empty(max(max_n, 1), dtype=np.uint64)
+        pp = np.empty(max(max_n, 1), dtype=np.uint64)
+        n = u64()
+        _check(load().sws_server_collect(self.handle, int(max_n), float(timeout), vp(ids.ctypes.data),
+                                         vp(cnt.ctypes.data), vp(hp.ctypes.data), vp(pp.ctypes.data),
+                                         vp(lat.ctypes.data), ctypes.byref(n)))
+        k = int(n.value)
+        return ids[:k], cnt[:k], lat[:k], hp[:k], pp[:k]
+
+    @staticmethod
+    def views(count: int, hash_ptr: int, pos_ptr: int):
+        """(keys, positions) uint32 arrays over a collected answer's pinned memory (no copy)."""
+        import numpy as np
+        if count == 0:
+            return np.zeros(0, np.uint32), np.zeros(0, np.uint32)
+        ht = ctypes.cast(int(hash_ptr), ctypes.POINTER(ctypes.c_uint32))
+        pt = ctypes.cast(int(pos_ptr), ctypes.POINTER(ctypes.c_uint32))
+        return np.ctypeslib.as_array(ht, shape=(int(count),)), np.ctypeslib.as_array(pt, shape=(int(count),))
+
+    def release(self, ids):
+        """Forget collected (or uncollected, answered) requests and free their result memory."""
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
+        _check(load().sws_server_release(self.handle, vp(a.ctypes.data), a.size))
 
     def stats(self) -> dict:
         st = ServerStats()
