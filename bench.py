@@ -39,7 +39,7 @@ METRIC = "minimizer Gbp/s & sliding-sum GB/s vs HBM peak; batched vs plain; p99 
 # elements (dram__bytes_read.sum + dram__bytes_write.sum, mean per launch), scaled to the run's n
 # by the elements processed.  Valid only for the kernel sources it was taken on: the hash below
 # covers them, and a mismatch reports the traffic as null.
-TRAFFIC_PROFILE = {"bytes_per_launch": 578324002.1, "n": 1 << 26, "sources_sha256_16": "f3f4b52f7d2da0f6",
+TRAFFIC_PROFILE = {"bytes_per_launch": 578392021.3, "n": 1 << 26, "sources_sha256_16": "7f8da2f2d001f10f",
                    "summary": "profiles/sliding_sum_sweep_2e26_dram_traffic.md"}
 TRAFFIC_SOURCES = ["paper_1811_10074_gb300/csrc/sliding_sum.cu", "paper_1811_10074_gb300/csrc/common.cuh",
                    "paper_1811_10074_gb300/csrc/tma.cuh"]
