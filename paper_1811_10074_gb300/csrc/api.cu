@@ -543,8 +543,9 @@ sws_status sws_build_table(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, 
   const uint64_t hbytes = round_up(sws::table_hist_words(m) * 4, 256);
   const uint64_t bbytes = round_up(sws::table_bsum_words(m) * 4, 256);
   const uint64_t gbytes = round_up(sws::table_gap_bytes(bucket_bits), 256);
+  const uint64_t mbytes = round_up(sws::table_msd_bytes(m), 256);
   const uint64_t copy_bytes = one_pass ? round_up(m * hs, 256) + round_up(m * 4, 256) : 0;
-  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256 + copy_bytes;
+  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256 + mbytes + copy_bytes;
   s = ensure_ws(ctx, total, st);
   if (s) return s;
   char *ws = static_cast<char *>(ctx->ws);
@@ -575,6 +576,7 @@ sws_status sws_build_table(sws_ctx *ctx, const uint8_t *seq, uint64_t n, int k, 
   a.ws_gaps = ws + 2 * kbytes + 2 * vbytes + hbytes + bbytes;
   a.ws_ngaps = reinterpret_cast<unsigned long long *>(ws + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes);
   a.gap_cap = sws::table_gap_capacity(bucket_bits);
+  a.ws_msd = ws + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256;
   cudaError_t e = sws::launch_table(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "seed-table launch");
   return SWS_OK;
@@ -654,7 +656,8 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
   const uint64_t hbytes = round_up(sws::table_hist_words(m) * 4, 256);
   const uint64_t bbytes = round_up(sws::table_bsum_words(m) * 4, 256);
   const uint64_t gbytes = round_up(sws::table_gap_bytes(bucket_bits), 256);
-  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256;
+  const uint64_t mbytes = round_up(sws::table_msd_bytes(m), 256);
+  const uint64_t total = 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256 + mbytes;
   s = ensure_ws(ctx, total, st);
   if (s) return s;
   char *w = static_cast<char *>(ctx->ws);
@@ -676,6 +679,7 @@ sws_status sws_kmer_table(sws_ctx *ctx, const void *hash, const uint32_t *pos, u
   a.ws_gaps = w + 2 * kbytes + 2 * vbytes + hbytes + bbytes;
   a.ws_ngaps = reinterpret_cast<unsigned long long *>(w + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes);
   a.gap_cap = sws::table_gap_capacity(bucket_bits);
+  a.ws_msd = w + 2 * kbytes + 2 * vbytes + hbytes + bbytes + gbytes + 256;
   cudaError_t e = sws::launch_table(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "seed-table launch");
   return SWS_OK;

@@ -156,11 +156,13 @@ struct TableArgs {
   void *ws_gaps;          // table_gap_bytes(bucket_bits)
   unsigned long long *ws_ngaps;
   uint64_t gap_cap;
+  void *ws_msd;  // table_msd_bytes(m): the segmented sort's descriptors (nullptr: LSD passes only)
 };
 uint64_t table_gap_capacity(int bucket_bits);
 uint64_t table_hist_words(uint64_t m);
 uint64_t table_bsum_words(uint64_t m);
 uint64_t table_gap_bytes(int bucket_bits);
+uint64_t table_msd_bytes(uint64_t m);
 cudaError_t launch_table(const TableArgs &a, cudaStream_t stream);
 
 // Seeding (seed.cu).
