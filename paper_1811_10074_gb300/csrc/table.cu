@@ -548,10 +548,10 @@ __global__ void k_bucket_starts(const SegInfo *__restrict__ seg, const uint32_t 
 
 // Pass C.  Bucket (g, d) -- records of X in input order -- is sorted in shared memory as 4-byte
 // items, (hash bits below the sub-bin) << 16 | index of the record within the bucket: a counting
-// sort into 2^BSUB_BITS sub-bins on the top remaining hash bits (shared-memory atomics, in any
-// order), then each sub-bin's few items by insertion sort, which orders equal hashes by index,
-// i.e. stably.  The j-th item's record, named by its index, is read again from X (by then in L2):
-// the full hash (g << (hash_bits - 8) | record >> 32) and the position (low word) go to the output.
+// sort into sub-bins on the top remaining hash bits (shared-memory atomics, in any order); then the
+// item at each place of a sub-bin, its record read again from X (by then in L2), goes to the
+// sub-bin's start plus its rank among the sub-bin's items, which orders equal hashes by index,
+// i.e. stably: the full hash (g << (hash_bits - 8) | record >> 32) and the position (low word).
 // A bucket of more than BCAP records is sorted the same way by a CTA that has an SM to itself
 // (k_bucket_big).  Buckets of more than BCAP2 records, or with a sub-bin of more than BCROWD (many
 // hits of a few hashes), take the LSD path.
@@ -608,14 +608,29 @@ __device__ __forceinline__ SubBins sub_bins(int hash_bits, PtrTable pt, int max_
   return S;
 }
 
-// Counts src[0, n) into the nr sub-bins from s_lo (count index sub - s_lo; records elsewhere are
-// skipped) and scans the counts into starts.  Returns, in every thread, whether a sub-bin holds
-// more than BCROWD records.
-template <int NT, uint32_t NSUB>
-__device__ bool count_scan(const unsigned long long *__restrict__ src, uint32_t n, const SubBins &S, uint32_t s_lo,
-                           uint32_t nr, uint32_t *cnt, uint32_t *s_w) {
+// Sub-bin counters: a 32-bit word each, or (PACK) a 16-bit half each, sub-bin c in half c & 1 of
+// word c >> 1 (the values stay below 2^16: a CTA that packs holds at most BCAP2 records).
+template <bool PACK>
+struct SubCnt {
+  uint32_t *w;
+  __device__ __forceinline__ uint32_t get(uint32_t c) const {
+    return PACK ? (w[c >> 1] >> ((c & 1u) << 4)) & 0xFFFFu : w[c];
+  }
+  __device__ __forceinline__ uint32_t bump(uint32_t c) const {  // the value before the increment
+    if (!PACK) return atomicAdd(&w[c], 1u);
+    const uint32_t sh = (c & 1u) << 4;
+    return (atomicAdd(&w[c >> 1], 1u << sh) >> sh) & 0xFFFFu;
+  }
+};
+
+// Counts src[0, n) into the sub-bins and scans the counts into starts.  Returns, in every thread,
+// whether a sub-bin holds more than BCROWD records.
+template <int NT, uint32_t NSUB, bool PACK>
+__device__ bool count_scan(const unsigned long long *__restrict__ src, uint32_t n, const SubBins &S,
+                           SubCnt<PACK> cnt, uint32_t *s_w) {
+  const uint32_t nr = S.nsub, nwords = PACK ? nr / 2 : nr;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (uint32_t i = t; i < nr; i += NT) cnt[i] = 0;
+  for (uint32_t i = t; i < nwords; i += NT) cnt.w[i] = 0;
   __syncthreads();
   // every loop over records issues BBATCH loads per thread before it uses them
   for (uint32_t i0 = t; i0 < n; i0 += NT * BBATCH) {
@@ -623,21 +638,21 @@ __device__ bool count_scan(const unsigned long long *__restrict__ src, uint32_t 
 #pragma unroll
     for (int q = 0; q < BBATCH; ++q) r[q] = i0 + q * NT < n ? src[i0 + q * NT] : 0ull;
 #pragma unroll
-    for (int q = 0; q < BBATCH; ++q) {
-      const uint32_t c = ((uint32_t)(r[q] >> S.sshift) & S.smask) - s_lo;
-      if (i0 + q * NT < n && c < nr) atomicAdd(&cnt[c], 1u);
-    }
+    for (int q = 0; q < BBATCH; ++q)
+      if (i0 + q * NT < n) cnt.bump((uint32_t)(r[q] >> S.sshift) & S.smask);
   }
   __syncthreads();
-  constexpr int LOC = (int)(NSUB / NT);
-  const uint32_t per = (nr + NT - 1) / NT;
+  // each thread a run of `per` counts (an even number of whole words when packed)
+  constexpr int LOC = (int)(NSUB / NT) > 2 ? (int)(NSUB / NT) : 2;
+  uint32_t per = (nr + NT - 1) / NT;
+  if (PACK && per < 2) per = 2;
   uint32_t loc[LOC];
   uint32_t tot = 0;
   bool crowd = false;
 #pragma unroll
   for (int q = 0; q < LOC; ++q) {
     const uint32_t i = t * per + q;
-    loc[q] = (q < (int)per && i < nr) ? cnt[i] : 0u;
+    loc[q] = (q < (int)per && i < nr) ? cnt.get(i) : 0u;
     crowd |= loc[q] > BCROWD;
     tot += loc[q];
   }
@@ -651,67 +666,82 @@ __device__ bool count_scan(const unsigned long long *__restrict__ src, uint32_t 
   uint32_t off = 0;
   for (int i = 0; i < warp; ++i) off += s_w[i];
   off += inc - tot;
+  if constexpr (PACK) {  // whole words: sub-bins i (even) and i + 1
 #pragma unroll
-  for (int q = 0; q < LOC; ++q) {
-    const uint32_t i = t * per + q;
-    if (q < (int)per && i < nr) cnt[i] = off;
-    off += loc[q];
+    for (int q = 0; q < LOC; q += 2) {
+      const uint32_t i = t * per + q;
+      if (q < (int)per && i < nr) cnt.w[i >> 1] = off | ((off + loc[q]) << 16);
+      off += loc[q] + loc[q + 1];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < LOC; ++q) {
+      const uint32_t i = t * per + q;
+      if (q < (int)per && i < nr) cnt.w[i] = off;
+      off += loc[q];
+    }
   }
   return __syncthreads_or(crowd);
 }
 
-// Places src's n records (their sub-bins in [s_lo, s_lo + nr), starts in cnt) as items, orders
-// each sub-bin, fills the table entries of these sub-bins and writes the output range
-// [start + out0, start + out0 + n).  A record's index within the bucket is its low 16 bits when
-// idx_in_record, else its place in src.  xb: the bucket's records in input order.
-template <int NT>
-__device__ void place_sort_write(const unsigned long long *__restrict__ src, uint32_t n, bool idx_in_record,
-                                 const SubBins &S, uint32_t s_lo, uint32_t nr, uint32_t *cnt, uint32_t *items,
-                                 const unsigned long long *__restrict__ xb, uint64_t start, uint32_t out0, uint32_t b,
+// Places src's n records (the bucket's records in input order; starts of the sub-bins in cnt)
+// as items by sub-bin, fills the table entries of the sub-bins, and writes the output range
+// [start + out0, start + out0 + n): the item at place j of sub-bin c goes to c's start + its rank
+// there (the number of smaller items: lower hash bits, or equal bits and a smaller index), so each
+// sub-bin comes out ordered by (hash, index) without being sorted in place.  The record an item
+// names is read again (from L2), for the output and for its sub-bin.
+template <int NT, bool PACK>
+__device__ void place_rank_write(const unsigned long long *__restrict__ src, uint32_t n, const SubBins &S,
+                                 SubCnt<PACK> cnt, uint32_t *items, uint64_t start, uint32_t out0, uint32_t b,
                                  int hash_bits, void *sorted_hash, uint32_t *sorted_pos, PtrTable pt) {
   const int t = threadIdx.x;
+  const uint32_t nr = S.nsub;
   for (uint32_t i0 = t; i0 < n; i0 += NT * BBATCH) {
     unsigned long long r[BBATCH];
 #pragma unroll
     for (int q = 0; q < BBATCH; ++q) r[q] = i0 + q * NT < n ? src[i0 + q * NT] : 0ull;
 #pragma unroll
     for (int q = 0; q < BBATCH; ++q) {
-      const uint32_t i = i0 + q * NT, c = ((uint32_t)(r[q] >> S.sshift) & S.smask) - s_lo;
-      if (i < n && c < nr)
-        items[atomicAdd(&cnt[c], 1u)] =
-            (((uint32_t)(r[q] >> 32) & S.lmask) << 16) | (idx_in_record ? (uint32_t)r[q] & 0xFFFFu : i);
+      const uint32_t i = i0 + q * NT, c = (uint32_t)(r[q] >> S.sshift) & S.smask;
+      if (i < n) items[cnt.bump(c)] = (((uint32_t)(r[q] >> 32) & S.lmask) << 16) | i;
     }
   }
   __syncthreads();
-  // cnt[c] now holds the end of sub-bin c; order each sub-bin's few items
-  for (uint32_t c = t; c < nr; c += NT) {
-    const uint32_t e = cnt[c], a0 = c ? cnt[c - 1] : 0u;
-    for (uint32_t i = a0 + 1; i < e; ++i) {
-      const uint32_t v = items[i];
-      uint32_t j = i;
-      while (j > a0 && items[j - 1] > v) {
-        items[j] = items[j - 1];
-        --j;
-      }
-      items[j] = v;
-    }
-  }
+  // each counter now holds the end of its sub-bin, i.e. the start of the next
   if (pt.e >= 0) {  // each table bucket starts where its first sub-bin does
     uint64_t *o = pt.offsets + ((uint64_t)b << pt.e);
-    for (uint32_t l = (s_lo >> S.align) + t; l < ((s_lo + nr) >> S.align); l += NT) {
-      const uint32_t f = (l << S.align) - s_lo;
-      o[l] = start + out0 + (f ? cnt[f - 1] : 0u);
+    for (uint32_t l = t; l < (nr >> S.align); l += NT) {
+      const uint32_t f = l << S.align;
+      o[l] = start + out0 + (f ? cnt.get(f - 1) : 0u);
     }
   }
-  __syncthreads();
-  const uint32_t g = b / SEG;
+  // the output from here, indexed by 32-bit places; the hash's top bits are the segment's
+  const unsigned long long hg = (unsigned long long)(b / SEG) << (hash_bits - 8);
+  const uint64_t o0 = start + out0;
+  unsigned long long *oh64 = static_cast<unsigned long long *>(sorted_hash) + o0;
+  uint32_t *oh32 = static_cast<uint32_t *>(sorted_hash) + o0, *op = sorted_pos + o0;
+  const bool wide = hash_bits > 32;
   for (uint32_t j0 = t; j0 < n; j0 += NT * BBATCH) {
+    uint32_t it[BBATCH];
     unsigned long long r[BBATCH];
 #pragma unroll
-    for (int q = 0; q < BBATCH; ++q) r[q] = j0 + q * NT < n ? xb[items[j0 + q * NT] & 0xFFFFu] : 0ull;
+    for (int q = 0; q < BBATCH; ++q) {
+      it[q] = j0 + q * NT < n ? items[j0 + q * NT] : 0u;
+      r[q] = j0 + q * NT < n ? src[it[q] & 0xFFFFu] : 0ull;
+    }
 #pragma unroll
-    for (int q = 0; q < BBATCH; ++q)
-      if (j0 + q * NT < n) bucket_write(r[q], start + out0 + j0 + q * NT, g, hash_bits, sorted_hash, sorted_pos);
+    for (int q = 0; q < BBATCH; ++q) {
+      if (j0 + q * NT < n) {
+        const uint32_t c = (uint32_t)(r[q] >> S.sshift) & S.smask;
+        const uint32_t a0 = c ? cnt.get(c - 1) : 0u, e = cnt.get(c);
+        uint32_t p = a0;
+        for (uint32_t k = a0; k < e; ++k) p += items[k] < it[q] ? 1u : 0u;
+        const unsigned long long h = hg | (r[q] >> 32);
+        if (wide) oh64[p] = h;
+        else oh32[p] = (uint32_t)h;
+        op[p] = (uint32_t)r[q];
+      }
+    }
   }
 }
 
@@ -772,12 +802,11 @@ __global__ void __launch_bounds__(BNT, 2) k_bucket_sort(const unsigned long long
   const uint32_t n = (uint32_t)n64;
   const unsigned long long *xb = X + start;
   const SubBins S = sub_bins(hash_bits, pt, BSUB_BITS);
-  if (count_scan<BNT, BNSUB>(xb, n, S, 0, S.nsub, cnt, s_w)) {
+  if (count_scan<BNT, BNSUB, false>(xb, n, S, SubCnt<false>{cnt}, s_w)) {
     if (t == 0) lists->list[atomicAdd(&lists->n, 1u)] = b;
     return;
   }
-  place_sort_write<BNT>(xb, n, false, S, 0, S.nsub, cnt, items, xb, start, 0, b, hash_bits, sorted_hash, sorted_pos,
-                        pt);
+  place_rank_write<BNT, false>(xb, n, S, SubCnt<false>{cnt}, items, start, 0, b, hash_bits, sorted_hash, sorted_pos, pt);
 }
 
 // A big bucket (more than BCAP records) by one CTA of BNT2 threads with the SM's shared memory to
@@ -798,12 +827,11 @@ __global__ void __launch_bounds__(BNT2, 1) k_bucket_big(const uint32_t *__restri
   const uint32_t n = (uint32_t)(bstart[b + 1] - start);
   const unsigned long long *xb = X + start;
   const SubBins S = sub_bins(hash_bits, pt, BSUB_BITS2);
-  if (n > BCAP2 || count_scan<BNT2, BNSUB2>(xb, n, S, 0, S.nsub, cnt, s_w)) {
+  if (n > BCAP2 || count_scan<BNT2, BNSUB2, false>(xb, n, S, SubCnt<false>{cnt}, s_w)) {
     if (threadIdx.x == 0) lists->list[atomicAdd(&lists->n, 1u)] = b;
     return;
   }
-  place_sort_write<BNT2>(xb, n, false, S, 0, S.nsub, cnt, items, xb, start, 0, b, hash_bits, sorted_hash, sorted_pos,
-                         pt);
+  place_rank_write<BNT2, false>(xb, n, S, SubCnt<false>{cnt}, items, start, 0, b, hash_bits, sorted_hash, sorted_pos, pt);
 }
 
 // Takes the next listed bucket (0xFFFFFFFF when none is left), the same for all threads.
