@@ -63,11 +63,12 @@ def parse_args():
     ap.add_argument("--keys-n", type=int, default=1 << 28, help="keys of the --section keys measurement")
     ap.add_argument("--keys-ws", default="4,5,6,7,8,9,10,11,12,13,14,15,16,17", help="window lengths of --section keys")
     ap.add_argument("--section", default="all",
-                    choices=["all", "sliding", "minimizers", "keys", "table", "batch", "serve"],
+                    choices=["all", "sliding", "minimizers", "keys", "table", "table-skew", "batch", "serve"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
     ap.add_argument("--genome-n", type=int, default=3_100_000_000, help="bases of the genome-scale table measurement")
+    ap.add_argument("--table-hits", type=int, default=100_000_000, help="hits of the --section table-skew measurement")
     args = ap.parse_args()
     args.ops = [o for o in args.ops.split(",") if o]
     args.ws = [int(v) for v in args.ws.split(",") if v]
@@ -583,6 +584,23 @@ def genome_table_extras(dev, ctx, n: int = 3_100_000_000, reps: int = 3, bucket_
     return out
 
 
+def table_skew_extras(dev, ctx, m: int, reps: int = 3, hash_bits: int = 38, bucket_bits: int = 24):
+    """Seed table of m synthetic 38-bit hits spread like w = 10 minimizer picks (small hashes far
+    more frequent) in the lowest quarter of the hash range, so that its buckets range from empty
+    to ~4x the genome's largest: the table sort alone, a few GB on the device."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    h = synth.minimizer_skew_hashes(m, hash_bits=hash_bits, w=10, drop_bits=2, device=dev)
+    p = torch.arange(m, dtype=torch.int32, device=dev)
+    tab = lambda: P.kmer_table(h, p, hash_bits, bucket_bits, ctx=ctx, stream=stream)
+    ms = time_call(tab, reps, stream)
+    return {"workload": f"{m} hits, {hash_bits}-bit hashes with the w=10 pick density in the lowest quarter "
+                        f"of the range, 2^{bucket_bits} buckets", "hits": m, "table_ms": round(ms, 3),
+            "table_mhits_s": round(m / (ms / 1e3) / 1e6, 1),
+            "algorithmic_gb_s": round(m * 24 / (ms / 1e3) / 1e9, 1)}
+
+
 def seeding_extras(seq, n, k, w, gh, gp, bucket_bits, ctx, stream, reps, n_reads: int = 1_000_000):
     """Seeding (Sec. 2.3) against the genome's seed table: 1e6 reads of 100-248 bases (multiples
     of 4) cut from the genome at byte boundaries, their minimizers in one batch, each minimizer
@@ -807,7 +825,7 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section in ("minimizers", "keys", "table", "batch", "serve"):
+    if args.section in ("minimizers", "keys", "table", "table-skew", "batch", "serve"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
@@ -822,6 +840,8 @@ def main():
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n, with_cpu=not args.no_cpu)}), flush=True)
             elif args.section == "table":
                 print(json.dumps({"genome_table": genome_table_extras(dev, ctx, args.genome_n)}), flush=True)
+            elif args.section == "table-skew":
+                print(json.dumps({"table_skew": table_skew_extras(dev, ctx, args.table_hits)}), flush=True)
             elif args.section == "batch":
                 print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
             else:

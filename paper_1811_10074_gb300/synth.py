@@ -41,6 +41,7 @@ STREAM_ARRIVAL = 9
 STREAM_REQ_LEN = 10
 STREAM_REQ_SEQ = 11
 STREAM_HASHES = 12
+STREAM_SKEW = 13
 
 
 def _s64(c: int) -> int:
@@ -250,6 +251,30 @@ def uint32_hashes(n: int, bits: int = 30, seed: int = 42, stream: int = STREAM_H
     """``n`` uniform ``bits``-bit values as int32 bit patterns (stand-in for a precomputed hash array)."""
     d = draws(seed, stream, n, device=device)
     return (_srl(d, 64 - bits)).to(torch.int64).to(torch.int32) if bits < 32 else _srl(d, 32).to(torch.int32)
+
+
+def minimizer_skew_hashes(m: int, hash_bits: int = 38, w: int = 10, drop_bits: int = 2, seed: int = 42,
+                          stream: int = STREAM_SKEW, device="cpu", chunk: int = 1 << 24) -> torch.Tensor:
+    """``m`` int64 hashes spread like the minimizer picks of i.i.d. keys.
+
+    A key at hash fraction x is some window's leftmost least key exactly when the keys to its
+    left that exceed it and the keys to its right that do not undercut it span at least w - 1
+    places, which for i.i.d. keys has probability (1 - x)^(w-1) (1 + (w-1) x): small hashes are
+    picked far more often than large ones.  Draw 2i gives x, draw 2i + 1 the acceptance test of
+    that density (rejection sampling); the hash is x scaled to [0, 2^(hash_bits - drop_bits)),
+    i.e. drop_bits > 0 crowds the hits into fewer buckets, as a genome 2^drop_bits times larger
+    would."""
+    out, have, start = [], 0, 0
+    scale = float(1 << (hash_bits - drop_bits))
+    while have < m:
+        d = draws(seed, stream, 2 * chunk, device=device, start=start)
+        start += 2 * chunk
+        x = _u53(d[0::2])
+        u = _u53(d[1::2])
+        keep = x[u < (1.0 - x) ** (w - 1) * (1.0 + (w - 1) * x)]
+        out.append((keep * scale).to(torch.int64))
+        have += keep.numel()
+    return torch.cat(out)[:m]
 
 
 # ----------------------------------------------------------------------------------------
