@@ -421,7 +421,9 @@ def e2e_leg(args, world, xs, outs, ctx, stream, step_bytes):
     del dy
     return {"value": round(world * step_bytes / (e_ms / 1e3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes["h2d"], "d2h_bytes_per_step": nbytes["d2h"], "ms_per_step": round(e_ms, 3),
-            "copies": "one stream per direction, two device output buffers per operator"}
+            "copies": "each distinct input array uploaded once per step and read there by every operator of "
+                      "its type (the one int32 array by add, min, max and xor); every output copied back; one "
+                      "stream per direction, two device output buffers per operator"}
 
 
 def time_call(fn, reps: int, stream):
@@ -451,7 +453,10 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     h, p, cnt = P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False)
     ms = time_call(lambda: P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False), 50, stream)
     out["plain_1e6"] = {"ms_per_call": round(ms, 4), "gbp_s": round(n / (ms / 1e3) / 1e9, 2),
-                        "picks": int(cnt.item()), "k": 15, "w": 10}
+                        "picks": int(cnt.item()), "k": 15, "w": 10,
+                        "per_call": "1 cudaMemsetAsync (tile status words) + 1 kernel (the look-back minimizer "
+                                    "kernel, below the size where the staged path pays off); no host sync; "
+                                    "output buffers from the caching allocator"}
     # long sequence: uniform bases (default 2^31), k=15 w=10, k=19 w=10, k=15 w=50
     n = long_n
     tag = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
