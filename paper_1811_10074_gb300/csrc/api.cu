@@ -468,6 +468,15 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
     if (e != cudaSuccess) return cuda_fail(e, "key minimizer launch");
     return SWS_OK;
   }
+  if (source == sws::SRC_DNA && !count_only && sws::dna_min_applies(seq, n, k, w, mode, n_nblocks)) {
+    // hashed k-mers, k <= 16, 4 <= w <= 17, no N-blocks: the single-pass kernel of keys_min.cu
+    s = ensure_ws(ctx, sws::keys_min_ws_bytes(n - (uint64_t)k + 1, w), st);
+    if (s) return s;
+    cudaError_t e = sws::launch_dna_min(seq, n, k, w, static_cast<uint32_t *>(hash_out), pos_out, capacity,
+                                        count_out, ctx->ws, ctx->d_err, ctx->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "DNA minimizer launch");
+    return SWS_OK;
+  }
   sws::MiniArgs a{};
   a.seq = seq;
   a.keys = keys;

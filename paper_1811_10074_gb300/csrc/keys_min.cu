@@ -44,6 +44,7 @@
 #include "../../include/sws.h"
 #include "common.cuh"
 #include "internal.h"
+#include "mini_common.cuh"
 #include "tma.cuh"
 
 namespace sws {
@@ -62,6 +63,7 @@ constexpr int KSLOTS = 3;                 // pick slots: a tile is placed two ti
 constexpr int KCAP = 2560;                // picks a slot holds (more: the tile is placed at once)
 constexpr int KSLOT_BYTES = KCAP * 8;     // (key, tile-relative position) per pick
 constexpr size_t KSMEM = 1024 + (size_t)KSTAGES * KSTAGE_STRIDE + (size_t)KSLOTS * KSLOT_BYTES;  // 2 CTAs/SM
+constexpr size_t KSMEM_DNA = 1024 + (size_t)KSLOTS * KSLOT_BYTES;  // the DNA form: pick slots only
 constexpr uint32_t ST_DONE = 0x80000000u;  // status: count published (low bits)
 constexpr uint32_t ST_FAIL = 0xC0000000u;  // status: the tile failed
 constexpr uint32_t ST_COUNT = 0x3FFFFFFFu;
@@ -77,6 +79,11 @@ struct KeysHeader {
 
 struct KeysArgs {
   const uint32_t *keys;
+  // DNA form: the 2-bit packed sequence (4-byte aligned, nbytes bytes) whose hashed canonical
+  // k-mers (k <= 16) are the keys
+  const uint8_t *seq;
+  uint64_t nbytes;
+  uint32_t k, kmask;
   uint32_t m;          // keys (at most 2^32 - 2^14, so that every index below fits 32 bits)
   uint32_t n_full;     // keys in whole 32-key rows (the tensor map's extent)
   uint32_t nwin;       // windows = m - w + 1
@@ -104,6 +111,24 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
 __device__ __forceinline__ int stage_offset(int q) {
   const int s = q + 32, row = s >> 5, col = s & 31;
   return row * 128 + ((((col >> 2) ^ (row & 7))) << 4) + ((col & 3) << 2);
+}
+
+// DNA form.  Packed word wi (bases 16 wi .. 16 wi + 15) of the sequence; bytes past its end read
+// as zero (the k-mers they would touch are past the last one and never used).
+__device__ __forceinline__ uint32_t seq_word(const KeysArgs &a, uint32_t wi) {
+  const uint64_t b = 4ull * wi;
+  if (b + 4 <= a.nbytes) return __ldg(reinterpret_cast<const uint32_t *>(a.seq) + wi);
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i)
+    if (b + i < a.nbytes) v |= (uint32_t)a.seq[b + i] << (8 * i);
+  return v;
+}
+// Key of the k-mer at position p: its hashed canonical value (0xFFFFFFFF past the last k-mer).
+__device__ __forceinline__ uint32_t dna_key(const KeysArgs &a, uint32_t p) {
+  if (p >= a.m) return 0xFFFFFFFFu;
+  const uint32_t wi = p >> 4;
+  const uint32_t v = __funnelshift_r(seq_word(a, wi), seq_word(a, wi + 1), 2 * (p & 15));  // bases p .. p+15
+  return mini::key_value32(mini::kmer32(v, (int)a.k, a.kmask), SWS_MINI_HASH, a.kmask);
 }
 
 // Minimum of every window j = 0..15 of a thread (keys X[j .. j+W-1]) and the thread-relative
@@ -268,7 +293,7 @@ __device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t c
   }
 }
 
-template <int W>
+template <int W, bool DNA>
 __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUtensorMap tmap, KeysArgs a) {
   extern __shared__ __align__(16) unsigned char ksm_raw[];
   __shared__ __align__(8) unsigned long long s_bar[KSTAGES];
@@ -280,7 +305,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   __shared__ unsigned long long s_red_sync[KNT / 32];
   __shared__ int s_flag_sync[KNT / 32];
   unsigned char *stages = ksm_raw + ((1024u - (tma::smem_u32(ksm_raw) & 1023u)) & 1023u);
-  unsigned char *slots = stages + KSTAGES * KSTAGE_STRIDE;
+  unsigned char *slots = stages + (DNA ? 0 : KSTAGES * KSTAGE_STRIDE);  // the DNA form stages nothing
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t T = a.num_tiles;
   constexpr uint32_t NONE = 0xFFFFFFFFu;
@@ -297,16 +322,18 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     failed = true;
   };
   if (t == 0) {
-    tma::prefetch_tensormap(&tmap);
+    if (!DNA) {
+      tma::prefetch_tensormap(&tmap);
 #pragma unroll
-    for (int s = 0; s < KSTAGES; ++s) tma::mbar_init(&s_bar[s], 1);
-    tma::fence_mbar_init();
+      for (int s = 0; s < KSTAGES; ++s) tma::mbar_init(&s_bar[s], 1);
+      tma::fence_mbar_init();
+    }
 #pragma unroll
     for (int s = 0; s < KSTAGES; ++s) {
       const uint32_t tk = atomicAdd(&a.hdr->ticket, 1u);
       s_tk[s] = tk;
-      s_issued[s] = tk < T;
-      if (tk < T) issue(s, tk);
+      s_issued[s] = !DNA && tk < T;
+      if (!DNA && tk < T) issue(s, tk);
     }
   }
   // thread 0 holds one ticket beyond the stages, taken a tile early so that the atomic's round
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     const uint32_t tile = s_tk[s];
     if (tile >= T) break;
     // ---- this tile's keys (each thread waits for the copy itself) ---------------------------------
-    const bool issued = s_issued[s] != 0 && !failed;  // a failed CTA waits for its copies at exit
+    const bool issued = !DNA && s_issued[s] != 0 && !failed;  // a failed CTA waits for its copies at exit
     // the counts before the oldest deferred tile (placed after this tile's barrier): two status
     // words per thread read now, so that the round trip overlaps this tile's work
     const bool pop = L == KSLOTS - 1 && !failed;
@@ -343,7 +370,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     uint32_t sv0 = 0, sv1 = 0;
     if (pop && j0 < (int)pt0) sv0 = ld_relaxed_u32(&a.status[j0]);
     if (pop && j0 + KNT < (int)pt0) sv1 = ld_relaxed_u32(&a.status[j0 + KNT]);
-    const bool ok = issued && tma::mbar_wait_bounded(&s_bar[s], (phases >> s) & 1u);
+    const bool ok = DNA || (issued && tma::mbar_wait_bounded(&s_bar[s], (phases >> s) & 1u));
     const bool wok = __all_sync(kFull, ok);
     const uint32_t tb = tile * (uint32_t)KTILE;  // first window (and key) of the tile
     const uint32_t g0 = tb + (uint32_t)q0;      // this thread's first window
@@ -351,37 +378,72 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     int mp[KWPT];
     unsigned mask = 0;  // windows that store a pick
     if (wok) {
-      const unsigned char *st = stages + s * KSTAGE_STRIDE;
       uint32_t X[32];
+      uint32_t xm1;
+      if constexpr (DNA) {
+        // keys of k-mers g0 .. g0+15 from packed words g0/16 and g0/16 + 1 (g0 is a multiple of 16);
+        // the next thread's first W-1 keys by shuffle, lane 31's from the extra k-mers of lanes
+        // 0 .. W-2 (the next warp's first W-1); lane 31's own extra k-mer is the one before the
+        // warp's first, which lane 0 needs (xm1).  Each lane hashes at most one extra k-mer.
+        const uint32_t wbase = g0 - (uint32_t)lane * KWPT;  // the warp's first k-mer
+        uint32_t pe = 0xFFFFFFFFu;
+        if (lane < W - 1) pe = wbase + (uint32_t)(32 * KWPT + lane);
+        else if (lane == 31 && wbase > 0) pe = wbase - 1;
+        const uint32_t extra = pe != 0xFFFFFFFFu ? dna_key(a, pe) : 0xFFFFFFFFu;
+        if (g0 + KWPT <= a.m && 4ull * ((g0 >> 4) + 2) <= a.nbytes) {
+          const uint32_t *sw = reinterpret_cast<const uint32_t *>(a.seq) + (g0 >> 4);
+          const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint4 u = *reinterpret_cast<const uint4 *>(st + base_a + ((c ^ r3a) << 4));
-        X[4 * c] = u.x;
-        X[4 * c + 1] = u.y;
-        X[4 * c + 2] = u.z;
-        X[4 * c + 3] = u.w;
-      }
-      constexpr int NU = (W - 1 + 3) / 4;  // 16-byte units of the next thread's keys needed
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c < NU) {
-          const uint4 u = *reinterpret_cast<const uint4 *>(st + base_b + ((c ^ r3b) << 4));
-          X[16 + 4 * c] = u.x;
-          X[16 + 4 * c + 1] = u.y;
-          X[16 + 4 * c + 2] = u.z;
-          X[16 + 4 * c + 3] = u.w;
+          for (int j = 0; j < KWPT; ++j)
+            X[j] = mini::key_value32(mini::kmer32(__funnelshift_r(v0, v1, 2 * j), (int)a.k, a.kmask), SWS_MINI_HASH,
+                                     a.kmask);
         } else {
-          X[16 + 4 * c] = X[16 + 4 * c + 1] = X[16 + 4 * c + 2] = X[16 + 4 * c + 3] = 0xFFFFFFFFu;
-        }
-      }
-      uint32_t xm1 = lane == 0 ? *reinterpret_cast<const uint32_t *>(st + stage_offset(q0 - 1)) : 0u;
-      if (g0 + KWPT + W - 1 > a.n_full) {  // keys of the final partial row (or past the end)
 #pragma unroll
-        for (int i = 0; i < KWPT + W - 1; ++i) {
-          const uint32_t gi = g0 + (uint32_t)i;
-          if (gi >= a.n_full) X[i] = gi < a.m ? a.keys[gi] : 0xFFFFFFFFu;
+          for (int j = 0; j < KWPT; ++j) X[j] = dna_key(a, g0 + (uint32_t)j);
         }
-        if (lane == 0 && g0 >= 1 && g0 - 1 >= a.n_full && g0 - 1 < a.m) xm1 = a.keys[g0 - 1];
+        xm1 = __shfl_sync(kFull, extra, 31);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (i < W - 1) {
+            const uint32_t dn = __shfl_down_sync(kFull, X[i], 1);
+            const uint32_t ex = __shfl_sync(kFull, extra, i);
+            X[KWPT + i] = lane == 31 ? ex : dn;
+          } else {
+            X[KWPT + i] = 0xFFFFFFFFu;
+          }
+        }
+      } else {
+        const unsigned char *st = stages + s * KSTAGE_STRIDE;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint4 u = *reinterpret_cast<const uint4 *>(st + base_a + ((c ^ r3a) << 4));
+          X[4 * c] = u.x;
+          X[4 * c + 1] = u.y;
+          X[4 * c + 2] = u.z;
+          X[4 * c + 3] = u.w;
+        }
+        constexpr int NU = (W - 1 + 3) / 4;  // 16-byte units of the next thread's keys needed
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < NU) {
+            const uint4 u = *reinterpret_cast<const uint4 *>(st + base_b + ((c ^ r3b) << 4));
+            X[16 + 4 * c] = u.x;
+            X[16 + 4 * c + 1] = u.y;
+            X[16 + 4 * c + 2] = u.z;
+            X[16 + 4 * c + 3] = u.w;
+          } else {
+            X[16 + 4 * c] = X[16 + 4 * c + 1] = X[16 + 4 * c + 2] = X[16 + 4 * c + 3] = 0xFFFFFFFFu;
+          }
+        }
+        xm1 = lane == 0 ? *reinterpret_cast<const uint32_t *>(st + stage_offset(q0 - 1)) : 0u;
+        if (g0 + KWPT + W - 1 > a.n_full) {  // keys of the final partial row (or past the end)
+#pragma unroll
+          for (int i = 0; i < KWPT + W - 1; ++i) {
+            const uint32_t gi = g0 + (uint32_t)i;
+            if (gi >= a.n_full) X[i] = gi < a.m ? a.keys[gi] : 0xFFFFFFFFu;
+          }
+          if (lane == 0 && g0 >= 1 && g0 - 1 >= a.n_full && g0 - 1 < a.m) xm1 = a.keys[g0 - 1];
+        }
       }
       window_minima<W>(X, mv, mp);
       // the pick of the window before this thread's first: the previous lane's last, shifted to
@@ -452,7 +514,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       const uint32_t nt = spare;
       spare = atomicAdd(&a.hdr->ticket, 1u);
       s_tk[s] = nt;
-      if (nt < T && !failed && !s_issued[s]) {
+      if (!DNA && nt < T && !failed && !s_issued[s]) {
         s_issued[s] = 1;
         tma::fence_proxy_async_smem();
         issue(s, nt);
@@ -589,29 +651,82 @@ EncodeTiledK encode_tiled_k() {
   return fn;
 }
 
-template <int W>
+template <int W, bool DNA>
 cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms, cudaStream_t st) {
-  auto kern = k_keys_min<W>;
+  auto kern = k_keys_min<W, DNA>;
+  constexpr size_t smem = DNA ? KSMEM_DNA : KSMEM;
   static int per_sm[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
   if (nb == 0) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KSMEM);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, KNT, KSMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, KNT, smem);
     if (e != cudaSuccess) return e;
     if (nb < 1) return cudaErrorInvalidConfiguration;
     if (dev >= 0 && dev < 64) per_sm[dev] = nb;
   }
   uint64_t grid = (uint64_t)num_sms * (uint64_t)nb;
   if (grid > a.num_tiles) grid = a.num_tiles;
-  kern<<<(unsigned)grid, KNT, KSMEM, st>>>(map, a);
+  kern<<<(unsigned)grid, KNT, smem, st>>>(map, a);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+bool dna_min_applies(const uint8_t *seq, uint64_t n, int k, int w, int mode, uint64_t n_nblocks) {
+  if (mode != SWS_MINI_HASH || k < 1 || k > 16 || w < 4 || w > KMAXW || n_nblocks != 0) return false;
+  if ((reinterpret_cast<uintptr_t>(seq) & 3u) != 0 || n < (uint64_t)k + 32) return false;
+  const uint64_t m = n - (uint64_t)k + 1;
+  return m <= (1ull << 32) - (1ull << 14) && (uint64_t)w <= m;
+}
+
+cudaError_t launch_dna_min(const uint8_t *seq, uint64_t n, int k, int w, uint32_t *key_out, uint32_t *pos_out,
+                           uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
+                           cudaStream_t st) {
+  if (!dna_min_applies(seq, n, k, w, SWS_MINI_HASH, 0)) return cudaErrorInvalidValue;
+  const uint64_t m = n - (uint64_t)k + 1;  // k-mers: the keys
+  const uint64_t nwin = m - (uint64_t)w + 1;
+  const uint64_t tiles = (nwin + KTILE - 1) / KTILE;
+  cudaError_t e = cudaMemsetAsync(ws, 0, keys_min_ws_bytes(m, w), st);
+  if (e != cudaSuccess) return e;
+  KeysArgs a{};
+  a.seq = seq;
+  a.nbytes = (n + 3) / 4;
+  a.k = (uint32_t)k;
+  a.kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+  a.m = (uint32_t)m;
+  a.n_full = (uint32_t)m;
+  a.nwin = (uint32_t)nwin;
+  a.num_tiles = (uint32_t)tiles;
+  a.hdr = static_cast<KeysHeader *>(ws);
+  a.status = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
+  a.key_out = key_out;
+  a.pos_out = pos_out;
+  a.capacity = capacity;
+  a.count_out = count_out;
+  a.err = err;
+  CUtensorMap none{};  // the DNA form has no tensor map
+  switch (w) {
+    case 4: return launch_w_keys<4, true>(none, a, num_sms, st);
+    case 5: return launch_w_keys<5, true>(none, a, num_sms, st);
+    case 6: return launch_w_keys<6, true>(none, a, num_sms, st);
+    case 7: return launch_w_keys<7, true>(none, a, num_sms, st);
+    case 8: return launch_w_keys<8, true>(none, a, num_sms, st);
+    case 9: return launch_w_keys<9, true>(none, a, num_sms, st);
+    case 10: return launch_w_keys<10, true>(none, a, num_sms, st);
+    case 11: return launch_w_keys<11, true>(none, a, num_sms, st);
+    case 12: return launch_w_keys<12, true>(none, a, num_sms, st);
+    case 13: return launch_w_keys<13, true>(none, a, num_sms, st);
+    case 14: return launch_w_keys<14, true>(none, a, num_sms, st);
+    case 15: return launch_w_keys<15, true>(none, a, num_sms, st);
+    case 16: return launch_w_keys<16, true>(none, a, num_sms, st);
+    case 17: return launch_w_keys<17, true>(none, a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 bool keys_min_applies(const uint32_t *keys, uint64_t m, int w) {
   return w >= 1 && w <= KMAXW && m >= 32 && m <= (1ull << 32) - (1ull << 14) && (uint64_t)w <= m &&
@@ -655,23 +770,23 @@ cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *k
   a.count_out = count_out;
   a.err = err;
   switch (w) {
-    case 1: return launch_w_keys<1>(map, a, num_sms, st);
-    case 2: return launch_w_keys<2>(map, a, num_sms, st);
-    case 3: return launch_w_keys<3>(map, a, num_sms, st);
-    case 4: return launch_w_keys<4>(map, a, num_sms, st);
-    case 5: return launch_w_keys<5>(map, a, num_sms, st);
-    case 6: return launch_w_keys<6>(map, a, num_sms, st);
-    case 7: return launch_w_keys<7>(map, a, num_sms, st);
-    case 8: return launch_w_keys<8>(map, a, num_sms, st);
-    case 9: return launch_w_keys<9>(map, a, num_sms, st);
-    case 10: return launch_w_keys<10>(map, a, num_sms, st);
-    case 11: return launch_w_keys<11>(map, a, num_sms, st);
-    case 12: return launch_w_keys<12>(map, a, num_sms, st);
-    case 13: return launch_w_keys<13>(map, a, num_sms, st);
-    case 14: return launch_w_keys<14>(map, a, num_sms, st);
-    case 15: return launch_w_keys<15>(map, a, num_sms, st);
-    case 16: return launch_w_keys<16>(map, a, num_sms, st);
-    case 17: return launch_w_keys<17>(map, a, num_sms, st);
+    case 1: return launch_w_keys<1, false>(map, a, num_sms, st);
+    case 2: return launch_w_keys<2, false>(map, a, num_sms, st);
+    case 3: return launch_w_keys<3, false>(map, a, num_sms, st);
+    case 4: return launch_w_keys<4, false>(map, a, num_sms, st);
+    case 5: return launch_w_keys<5, false>(map, a, num_sms, st);
+    case 6: return launch_w_keys<6, false>(map, a, num_sms, st);
+    case 7: return launch_w_keys<7, false>(map, a, num_sms, st);
+    case 8: return launch_w_keys<8, false>(map, a, num_sms, st);
+    case 9: return launch_w_keys<9, false>(map, a, num_sms, st);
+    case 10: return launch_w_keys<10, false>(map, a, num_sms, st);
+    case 11: return launch_w_keys<11, false>(map, a, num_sms, st);
+    case 12: return launch_w_keys<12, false>(map, a, num_sms, st);
+    case 13: return launch_w_keys<13, false>(map, a, num_sms, st);
+    case 14: return launch_w_keys<14, false>(map, a, num_sms, st);
+    case 15: return launch_w_keys<15, false>(map, a, num_sms, st);
+    case 16: return launch_w_keys<16, false>(map, a, num_sms, st);
+    case 17: return launch_w_keys<17, false>(map, a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -314,3 +314,31 @@ def test_generic_staged_path(k, w):
     rh, rp, rpo = oracle.minimizers_batch(bseq, offs, k, w)
     assert (bpo.cpu().numpy().view(np.uint64) == rpo).all()
     assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
+
+
+# The single-pass kernel on packed bases (hashed k-mers, k <= 16, 4 <= w <= 17, no N-blocks, the
+# sequence 4-byte aligned): each thread hashes 16 k-mers; a warp's halo k-mers are hashed by its
+# first w-1 lanes and its previous k-mer by lane 31.  Lengths around tiles of 4096 windows, ties
+# from low-complexity sequences, and an unaligned view that takes the staged path instead.
+@pytest.mark.parametrize("w", list(range(4, 18)))
+def test_dna_single_pass_kernel(w):
+    rng = np.random.default_rng(3000 + w)
+    for k in (1, 2, 7, 15, 16):
+        span = k + w - 1
+        for n in (k + 32, span + 4095, span + 4096, span + 4097, span + 3 * 4096 + 1, 2_000_003):
+            seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+            check_minimizers(seq, n, k, w, "hash")
+    n = 300_001
+    for name, codes in (("constant", np.zeros(n, np.uint8)),
+                        ("period 3", np.tile(np.array([0, 1, 3], np.uint8), n // 3 + 1)[:n]),
+                        ("two letters", rng.integers(0, 2, size=n).astype(np.uint8))):
+        seq = synth.pack_codes(torch.from_numpy(codes))
+        for k in (5, 16):
+            check_minimizers(seq, n, k, w, "hash")
+    # a view starting one byte in (bases 4 .. n+3): not 4-byte aligned, so the staged kernel runs
+    n = 50_000
+    full = synth.acgt_uniform_packed(n + 8, seed=w)
+    fd = full.cuda()
+    h, p = B.minimizers(fd[1:], n, 15, w)
+    rh, rp = oracle.minimizers(full[1:].clone(), n, 15, w)
+    assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
