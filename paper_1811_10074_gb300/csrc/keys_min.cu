@@ -393,10 +393,16 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         if (g0 + KWPT <= a.m && 4ull * ((g0 >> 4) + 2) <= a.nbytes) {
           const uint32_t *sw = reinterpret_cast<const uint32_t *>(a.seq) + (g0 >> 4);
           const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1);
+          // the 32 bases reversed once (base i at bits 62 - 2i of rhi:rlo): the forward k-mer at j
+          // is then one funnel shift and one shift, with no per-k-mer reversal
+          const uint32_t rhi = mini::rev_pairs32(v0), rlo = mini::rev_pairs32(v1);
+          const int fsh = 32 - 2 * (int)a.k;
 #pragma unroll
-          for (int j = 0; j < KWPT; ++j)
-            X[j] = mini::key_value32(mini::kmer32(__funnelshift_r(v0, v1, 2 * j), (int)a.k, a.kmask), SWS_MINI_HASH,
-                                     a.kmask);
+          for (int j = 0; j < KWPT; ++j) {
+            const uint32_t rc = ~__funnelshift_r(v0, v1, 2 * j) & a.kmask;
+            const uint32_t fw = (j == 0 ? rhi : __funnelshift_r(rlo, rhi, 32 - 2 * j)) >> fsh;
+            X[j] = mini::wang_mix32(fw < rc ? fw : rc, a.kmask);
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < KWPT; ++j) X[j] = dna_key(a, g0 + (uint32_t)j);
