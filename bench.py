@@ -454,9 +454,9 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     ms = time_call(lambda: P.minimizers(seq, n, 15, 10, ctx=ctx, stream=stream, sync=False), 50, stream)
     out["plain_1e6"] = {"ms_per_call": round(ms, 4), "gbp_s": round(n / (ms / 1e3) / 1e9, 2),
                         "picks": int(cnt.item()), "k": 15, "w": 10,
-                        "per_call": "1 cudaMemsetAsync (tile status words) + 1 kernel (the look-back minimizer "
-                                    "kernel, below the size where the staged path pays off); no host sync; "
-                                    "output buffers from the caching allocator"}
+                        "per_call": "1 cudaMemsetAsync (workspace header and tile status words) + 1 kernel "
+                                    "(the single-pass kernel on packed bases: 245 tiles, one per CTA); no host "
+                                    "sync; output buffers from the caching allocator"}
     # long sequence: uniform bases (default 2^31), k=15 w=10, k=19 w=10, k=15 w=50
     n = long_n
     tag = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)

@@ -22,7 +22,8 @@
 // differs from the previous window's, or equals it while the previous pick was the previous
 // window's first key (which has left).
 //
-// Order.  Tiles are handed out by an atomic ticket, in order, and each CTA takes its tickets in
+// Order.  CTA b of G takes tiles b, b + G and b + 2G first (so that an input of a few tiles per CTA
+// is spread evenly), then tiles 3G, 3G + 1, ... by an atomic ticket, so each CTA takes its tiles in
 // increasing order.  A tile's pick count goes to its status word as soon as it is known; the
 // tile's picks wait in one of three shared-memory slots while the CTA computes its next two
 // tiles, and then the CTA finds their output offset as the end of its own previous tile's picks
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     }
 #pragma unroll
     for (int s = 0; s < KSTAGES; ++s) {
-      const uint32_t tk = atomicAdd(&a.hdr->ticket, 1u);
+      const uint32_t tk = blockIdx.x + (uint32_t)s * gridDim.x;
       s_tk[s] = tk;
       s_issued[s] = !DNA && tk < T;
       if (!DNA && tk < T) issue(s, tk);
@@ -338,7 +339,8 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   }
   // thread 0 holds one ticket beyond the stages, taken a tile early so that the atomic's round
   // trip is not on the path of a refill
-  uint32_t spare = t == 0 ? atomicAdd(&a.hdr->ticket, 1u) : 0u;
+  const uint32_t first_dyn = (uint32_t)KSTAGES * gridDim.x;  // the first ticket handed out dynamically
+  uint32_t spare = t == 0 ? first_dyn + atomicAdd(&a.hdr->ticket, 1u) : 0u;
   __syncthreads();
 
   uint32_t phases = 0;             // bit s: parity of stage s's next completion
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     if (t == 0) {
       st_relaxed_u32(&a.status[tile], failed ? ST_FAIL : (ST_DONE | tot));
       const uint32_t nt = spare;
-      spare = atomicAdd(&a.hdr->ticket, 1u);
+      spare = first_dyn + atomicAdd(&a.hdr->ticket, 1u);
       s_tk[s] = nt;
       if (!DNA && nt < T && !failed && !s_issued[s]) {
         s_issued[s] = 1;

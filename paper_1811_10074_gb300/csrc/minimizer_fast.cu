@@ -224,19 +224,45 @@ __global__ void __launch_bounds__(FNT) k_mini_stage(MiniArgs a, uint64_t nwin, i
       // one loop per key mode, so the mode test is not repeated for every k-mer
       auto keys = [&](auto mode_c) {
         constexpr int MODE = decltype(mode_c)::value;
+        // The thread's bases are reversed once (2-bit groups, words swapped): the forward k-mer at
+        // offset j is then a funnel shift of the reversed words by a constant and one shift by a
+        // k-dependent amount, with no per-k-mer reversal; the reverse complement is the
+        // complemented window itself.
         if (sizeof(V) == 4) {
           const uint32_t kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+          const uint32_t rhi = rev_pairs32(v0), rlo = rev_pairs32(v1);  // base i at bit 62 - 2i
+          const int fsh = 32 - 2 * k;
 #pragma unroll
-          for (int j = 0; j < VPT; ++j)
-            x[j] = (V)key_value32(kmer32(__funnelshift_r(v0, v1, 2 * j), k, kmask), MODE, kmask);
+          for (int j = 0; j < VPT; ++j) {
+            const uint32_t fw = (j == 0 ? rhi : __funnelshift_r(rlo, rhi, 32 - 2 * j)) >> fsh;
+            if (MODE == SWS_MINI_FWD) {
+              x[j] = (V)fw;
+            } else {
+              const uint32_t rc = ~__funnelshift_r(v0, v1, 2 * j) & kmask;
+              const uint32_t c = fw < rc ? fw : rc;
+              x[j] = (V)(MODE == SWS_MINI_CANONICAL ? c : wang_mix32(c, kmask));
+            }
+          }
         } else {
           const uint32_t v2 = __funnelshift_r(sw[q + 2], sw[q + 3], s);
           const unsigned long long kmask = 2 * k == 64 ? ~0ull : ((1ull << (2 * k)) - 1ull);
+          const uint32_t r2 = rev_pairs32(v0), r1 = rev_pairs32(v1), r0 = rev_pairs32(v2);  // base i at bit 94 - 2i
+          const int fsh = 64 - 2 * k;  // 0 .. 30: 2k > 32 here
 #pragma unroll
           for (int j = 0; j < VPT; ++j) {
-            const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
-                                           __funnelshift_r(v0, v1, 2 * j);
-            x[j] = (V)key_value64_wide(kmer64(w64, k, kmask), MODE, (uint32_t)(kmask >> 32));  // 2k > 32 here
+            const uint32_t lo = j == 0 ? r1 : __funnelshift_r(r0, r1, 32 - 2 * j);  // bases j+31 .. j+16
+            const uint32_t hi = j == 0 ? r2 : __funnelshift_r(r1, r2, 32 - 2 * j);  // bases j+15 .. j
+            const unsigned long long fw =
+                ((unsigned long long)(hi >> fsh) << 32) | __funnelshift_r(lo, hi, fsh);
+            if (MODE == SWS_MINI_FWD) {
+              x[j] = (V)fw;
+            } else {
+              const unsigned long long w64 = ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) |
+                                             __funnelshift_r(v0, v1, 2 * j);
+              const unsigned long long rc = ~w64 & kmask;
+              const unsigned long long c = fw < rc ? fw : rc;
+              x[j] = (V)(MODE == SWS_MINI_CANONICAL ? c : wang_mix64_wide(c, (uint32_t)(kmask >> 32)));
+            }
           }
         }
       };
