@@ -63,12 +63,13 @@ def parse_args():
     ap.add_argument("--keys-n", type=int, default=1 << 28, help="keys of the --section keys measurement")
     ap.add_argument("--keys-ws", default="4,5,6,7,8,9,10,11,12,13,14,15,16,17", help="window lengths of --section keys")
     ap.add_argument("--section", default="all",
-                    choices=["all", "sliding", "minimizers", "keys", "table", "table-skew", "batch", "serve"],
+                    choices=["all", "sliding", "minimizers", "fused", "keys", "table", "table-skew", "batch", "serve"],
                     help="'minimizers' runs only the secondary minimizer measurements")
     ap.add_argument("--cpu-sample", type=int, default=1 << 20, help="elements per case for the CPU baseline")
     ap.add_argument("--mini-n", type=int, default=1 << 31, help="bases of the long minimizer measurement")
     ap.add_argument("--genome-n", type=int, default=3_100_000_000, help="bases of the genome-scale table measurement")
     ap.add_argument("--table-hits", type=int, default=100_000_000, help="hits of the --section table-skew measurement")
+    ap.add_argument("--fused", default="15,10", help="k,w of the --section fused measurement (--mini-n bases)")
     args = ap.parse_args()
     args.ops = [o for o in args.ops.split(",") if o]
     args.ws = [int(v) for v in args.ws.split(",") if v]
@@ -462,14 +463,7 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     tag = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
     seq = synth.acgt_uniform_packed(n, seed=43, device=dev)
     for k, w in ((15, 10), (19, 10), (15, 50)):
-        cap = int(n * 2.6 / (w + 1)) + 1024
-        ms = time_call(lambda: P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False), 3, stream)
-        _, _, cnt = P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
-        picks = int(cnt.item())
-        hb = 4 if 2 * k <= 32 else 8
-        bytes_ = n / 4 + picks * (hb + 4)
-        out[f"fused_{tag}_k{k}_w{w}"] = {"ms": round(ms, 3), "gbp_s": round(n / (ms / 1e3) / 1e9, 1),
-                                        "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
+        out[f"fused_{tag}_k{k}_w{w}"] = fused_case(dev, ctx, n, k, w, seq=seq)
     del seq
     torch.cuda.empty_cache()
     # paper-equivalent (Sec. 4): sliding minimum over the hashed canonical 15-mers of a uniform
@@ -484,6 +478,23 @@ def minimizer_extras(dev, ctx, long_n: int = 1 << 31, with_cpu: bool = True):
     if with_cpu:
         out["cpu_baseline"] = minimizer_cpu_baseline(keys, m, sweep)
     return out
+
+
+def fused_case(dev, ctx, n: int, k: int, w: int, seq=None, reps: int = 3):
+    """Minimizers of n uniform bases (seed 43) in one call: one warm-up call, then reps timed."""
+    import paper_1811_10074_gb300 as P
+    from paper_1811_10074_gb300 import synth
+    stream = torch.cuda.current_stream()
+    if seq is None:
+        seq = synth.acgt_uniform_packed(n, seed=43, device=dev)
+    cap = int(n * 2.6 / (w + 1)) + 1024
+    ms = time_call(lambda: P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False), reps, stream)
+    _, _, cnt = P.minimizers(seq, n, k, w, capacity=cap, ctx=ctx, stream=stream, sync=False)
+    picks = int(cnt.item())
+    hb = 4 if 2 * k <= 32 else 8
+    bytes_ = n / 4 + picks * (hb + 4)
+    return {"ms": round(ms, 3), "gbp_s": round(n / (ms / 1e3) / 1e9, 1),
+            "hbm_gbs": round(bytes_ / (ms / 1e3) / 1e9, 1), "picks": picks}
 
 
 def keys_sweep(dev, ctx, m: int, ws, reps: int = 5):
@@ -835,7 +846,7 @@ def main():
             return
         print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
-    if args.section in ("minimizers", "keys", "table", "table-skew", "batch", "serve"):
+    if args.section in ("minimizers", "fused", "keys", "table", "table-skew", "batch", "serve"):
         from paper_1811_10074_gb300 import build as B
         import paper_1811_10074_gb300 as P
         B.build()
@@ -846,6 +857,9 @@ def main():
                 ws = [int(v) for v in args.keys_ws.split(",") if v]
                 _, sweep = keys_sweep(dev, ctx, args.keys_n, ws)
                 print(json.dumps({"keys": {"n": args.keys_n, "sweep": sweep}}), flush=True)
+            elif args.section == "fused":
+                k, w = (int(v) for v in args.fused.split(","))
+                print(json.dumps({"fused": fused_case(dev, ctx, args.mini_n, k, w)}), flush=True)
             elif args.section == "minimizers":
                 print(json.dumps({"minimizers": minimizer_extras(dev, ctx, args.mini_n, with_cpu=not args.no_cpu)}), flush=True)
             elif args.section == "table":
