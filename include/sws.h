@@ -223,10 +223,12 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
  * graph (one persistent minimizer launch plus its scan, gather and fix-up kernels) whatever the
  * size of the batch, reading the sizes from a device descriptor.  Results are those of
  * sws_minimizers_batch on the same reads.
- *   options: SWS_BATCH_DEFAULT takes the staged path (the staged kernel for 4 <= w <= 256 and
- *            k <= 32, otherwise the generic kernel writing per-tile slots, then a scan and a
- *            gather), SWS_BATCH_TUNE times it against the single-kernel look-back path on a
- *            synthetic batch of the largest size and keeps the faster (see sws_batch_io.tuned_ms),
+ *   options: SWS_BATCH_DEFAULT takes the single-pass kernel for hashed k-mers with k <= 16 and
+ *            4 <= w <= 17 (one launch: picks placed in order from per-tile counts), otherwise the
+ *            staged path (the staged kernel for 4 <= w <= 256 and k <= 32, otherwise the generic
+ *            kernel writing per-tile slots, then a scan and a gather); SWS_BATCH_TUNE times every
+ *            applicable path, the single-kernel look-back path included, on a synthetic batch of
+ *            the largest size and keeps the fastest (see sws_batch_io.tuned_ms);
  *            SWS_BATCH_LOOKBACK forces the look-back path.
  * One run may be in flight per object: sws_batch_run waits for the previous run to finish before
  * it overwrites the descriptor.  Use one object per concurrent stream. */
@@ -243,8 +245,8 @@ typedef struct sws_batch_io {
   uint64_t *count;         /* device output: number of picks                                    */
   uint64_t capacity;       /* entries of hash/pos (= max_bases, never exceeded)                  */
   uint64_t max_reads, max_bases;
-  int path;                /* 0: kernel specialized on w, 1: look-back kernel                    */
-  float tuned_ms[2];       /* measured ms per largest batch for each path (-1: not timed)        */
+  int path;                /* 0: staged kernel, 1: look-back kernel, 2: single-pass kernel       */
+  float tuned_ms[3];       /* measured ms per largest batch for each path (-1: not timed)        */
 } sws_batch_io;
 sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases, int k, int w, int mode,
                             int options, sws_batch **out);

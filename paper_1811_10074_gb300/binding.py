@@ -93,7 +93,7 @@ class ServerStats(ctypes.Structure):
 class BatchIO(ctypes.Structure):
     _fields_ = [("seq", vp), ("offsets", vp), ("hash", vp), ("pos", vp), ("pick_offsets", vp), ("count", vp),
                 ("capacity", u64), ("max_reads", u64), ("max_bases", u64), ("path", i32),
-                ("tuned_ms", ctypes.c_float * 2)]
+                ("tuned_ms", ctypes.c_float * 3)]
 
 
 def library_path() -> str:
@@ -415,7 +415,7 @@ class Batch:
         self.pick_offsets = torch.as_tensor(_DevArray(io.pick_offsets, (int(max_reads) + 1,), "<i8"), device=dev)
         self.count = torch.as_tensor(_DevArray(io.count, (1,), "<i8"), device=dev)
         self.path = int(io.path)
-        self.tuned_ms = (float(io.tuned_ms[0]), float(io.tuned_ms[1]))
+        self.tuned_ms = tuple(float(v) for v in io.tuned_ms)
         self.nreads = 0
 
     def close(self):

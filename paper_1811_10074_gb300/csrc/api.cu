@@ -468,12 +468,23 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
     if (e != cudaSuccess) return cuda_fail(e, "key minimizer launch");
     return SWS_OK;
   }
-  if (source == sws::SRC_DNA && !count_only && sws::dna_min_applies(seq, n, k, w, mode, n_nblocks)) {
-    // hashed k-mers, k <= 16, 4 <= w <= 17, no N-blocks: the single-pass kernel of keys_min.cu
-    s = ensure_ws(ctx, sws::keys_min_ws_bytes(n - (uint64_t)k + 1, w), st);
+  if (source == sws::SRC_DNA && !count_only && sws::dna_min_applies(seq, n, k, w, mode)) {
+    // hashed k-mers, k <= 16, 4 <= w <= 17: the single-pass kernel of keys_min.cu
+    s = ensure_ws(ctx, sws::dna_min_ws_bytes(n, k, w), st);
     if (s) return s;
-    cudaError_t e = sws::launch_dna_min(seq, n, k, w, static_cast<uint32_t *>(hash_out), pos_out, capacity,
-                                        count_out, ctx->ws, ctx->d_err, ctx->num_sms, st);
+    sws::DnaMinArgs d{};
+    d.seq = seq;
+    d.n = n;
+    d.k = k;
+    d.w = w;
+    d.barrier = n_nblocks > 0 ? sws::BAR_NBLOCK : -1;
+    d.bar = nblocks;
+    d.nbar = n_nblocks;
+    d.key_out = static_cast<uint32_t *>(hash_out);
+    d.pos_out = pos_out;
+    d.capacity = capacity;
+    d.count_out = count_out;
+    cudaError_t e = sws::launch_dna_min(d, ctx->ws, ctx->d_err, ctx->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e, "DNA minimizer launch");
     return SWS_OK;
   }
@@ -618,6 +629,32 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
   }
   if (!seq) return fail(SWS_ERR_INVALID, "seq is NULL");
   SWS_CUDA(cudaMemsetAsync(pick_offsets, 0xff, (nreads + 1) * sizeof(uint64_t), st));
+  const uint64_t fix_blocks = (nreads + 1023) / 1024 + 1;
+  if (sws::dna_min_applies(seq, total_bases, k, w, mode)) {
+    // hashed k-mers, k <= 16, 4 <= w <= 17: the single-pass kernel with read starts as barriers
+    const uint64_t dws = (sws::dna_min_ws_bytes(total_bases, k, w) + 255) / 256 * 256;
+    s = ensure_ws(ctx, dws + fix_blocks * 8, st);
+    if (s) return s;
+    sws::DnaMinArgs d{};
+    d.seq = seq;
+    d.n = total_bases;
+    d.k = k;
+    d.w = w;
+    d.barrier = sws::BAR_READS;
+    d.bar = base_offsets;
+    d.nbar = nreads;
+    d.pick_offsets = pick_offsets;
+    d.key_out = static_cast<uint32_t *>(hash_out);
+    d.pos_out = pos_out;
+    d.capacity = capacity;
+    d.count_out = count_out;
+    cudaError_t e = sws::launch_dna_min(d, ctx->ws, ctx->d_err, ctx->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "DNA minimizer launch");
+    e = sws::launch_pick_offsets_fixup(pick_offsets, nreads, count_out,
+                                       reinterpret_cast<uint64_t *>(static_cast<char *>(ctx->ws) + dws), st);
+    if (e != cudaSuccess) return cuda_fail(e, "pick-offset fix-up launch");
+    return SWS_OK;
+  }
   sws::MiniArgs a{};
   a.seq = seq;
   a.n = total_bases;
@@ -631,7 +668,6 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
   a.capacity = capacity;
   a.count_out = count_out;
   a.pick_offsets = pick_offsets;
-  const uint64_t fix_blocks = (nreads + 1023) / 1024 + 1;
   void *fix = nullptr;
   s = run_minimizers(ctx, a, sws::SRC_DNA, sws::BAR_READS, nwin, fix_blocks * 8, &fix, st);
   if (s) return s;

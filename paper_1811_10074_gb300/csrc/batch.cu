@@ -5,9 +5,10 @@
 //
 // A graph's launch arguments are fixed, so the kernels are launched for the largest batch the
 // object was created for and read the actual sizes (reads, bases, windows, tiles) from a small
-// device descriptor that the graph's first node copies from pinned host memory.  The tiling and
-// the algorithm (the staged kernel specialized on w, or the single-kernel look-back path) are
-// chosen by timing both graphs on a synthetic batch of the largest size when the object is made.
+// device descriptor that the graph's first node copies from pinned host memory.  The algorithm is
+// the single-pass kernel (hashed k-mers, k <= 16, 4 <= w <= 17), else the staged kernel
+// specialized on w; on request every applicable graph, the single-kernel look-back path included,
+// is timed on a synthetic batch of the largest size when the object is made and the fastest kept.
 #include <cstdio>
 #include <cstring>
 
@@ -34,16 +35,16 @@ struct sws_batch {
   uint64_t ws_bytes = 0;
   int *d_err = nullptr;
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // per path
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // per path
   int path = -1;                                  // sws::BatchPath
-  float tuned_ms[2] = {-1.f, -1.f};
+  float tuned_ms[3] = {-1.f, -1.f, -1.f};
   cudaEvent_t done = nullptr;
   bool launched = false;
 };
 
 namespace {
 
-enum BatchPath { PATH_STAGED = 0, PATH_LOOKBACK = 1 };
+enum BatchPath { PATH_STAGED = 0, PATH_LOOKBACK = 1, PATH_SINGLE = 2 };
 
 uint64_t rup(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
@@ -66,6 +67,8 @@ struct Layout {
   uint64_t counts, scan, tilebar, shash, spos, sfirst, fix;
   // look-back
   uint64_t status, counter, ltilebar, lfix;
+  // single pass
+  uint64_t sfix;
 };
 
 Layout layout_for(const sws_batch *b, int path) {
@@ -73,7 +76,12 @@ Layout layout_for(const sws_batch *b, int path) {
   const uint64_t span = (uint64_t)(b->w + b->k - 1);
   const uint64_t nwin = b->max_bases >= span ? b->max_bases - span + 1 : 0;
   const uint64_t fixb = ((b->max_reads + 1023) / 1024 + 1) * 8;
-  if (path == PATH_STAGED) {
+  if (path == PATH_SINGLE) {
+    const uint64_t tw = (uint64_t)sws::dna_min_tile_windows();
+    L.tiles = (nwin + tw - 1) / tw;
+    L.sfix = rup(sws::dna_min_ws_bytes(b->max_bases, b->k, b->w), 256);
+    L.bytes = L.sfix + rup(fixb, 256);
+  } else if (path == PATH_STAGED) {
     const uint64_t tw = (uint64_t)sws::mini_staged_tile_windows(sws::SRC_DNA, b->k, b->w);
     L.tiles = (nwin + tw - 1) / tw;
     const uint64_t slots = L.tiles * tw;
@@ -121,7 +129,24 @@ sws_status enqueue(sws_batch *b, int path, cudaStream_t st) {
   a.desc = b->d_desc;
   uint64_t *fix;
   cudaError_t e;
-  if (path == PATH_STAGED) {
+  if (path == PATH_SINGLE) {
+    sws::DnaMinArgs d{};
+    d.seq = b->seq;
+    d.n = b->max_bases;
+    d.k = b->k;
+    d.w = b->w;
+    d.barrier = sws::BAR_READS;
+    d.bar = b->offsets;
+    d.nbar = b->max_reads;
+    d.pick_offsets = b->pick_offsets;
+    d.desc = b->d_desc;
+    d.key_out = static_cast<uint32_t *>(b->hash);
+    d.pos_out = b->pos;
+    d.capacity = b->capacity;
+    d.count_out = b->count;
+    fix = reinterpret_cast<uint64_t *>(ws + L.sfix);
+    e = sws::launch_dna_min(d, ws, b->d_err, b->ctx->num_sms, st);
+  } else if (path == PATH_STAGED) {
     a.tile_counts = reinterpret_cast<uint32_t *>(ws + L.counts);
     a.scan_tmp = reinterpret_cast<uint32_t *>(ws + L.scan);
     a.tile_bar = reinterpret_cast<uint2 *>(ws + L.tilebar);
@@ -147,8 +172,9 @@ sws_status enqueue(sws_batch *b, int path, cudaStream_t st) {
 void set_desc(sws_batch *b, int path, uint64_t nreads, uint64_t total) {
   const uint64_t span = (uint64_t)(b->w + b->k - 1);
   const uint64_t nwin = (nreads > 0 && total >= span) ? total - span + 1 : 0;
-  const uint64_t tw =
-      (uint64_t)(path == PATH_STAGED ? sws::mini_staged_tile_windows(sws::SRC_DNA, b->k, b->w) : sws::mini_tile_windows(b->w));
+  const uint64_t tw = (uint64_t)(path == PATH_SINGLE   ? sws::dna_min_tile_windows()
+                                 : path == PATH_STAGED ? sws::mini_staged_tile_windows(sws::SRC_DNA, b->k, b->w)
+                                                       : sws::mini_tile_windows(b->w));
   const uint64_t tiles = (nwin + tw - 1) / tw;
   memset(b->h_desc, 0, sws::BD_WORDS * 8);
   b->h_desc[sws::BD_NREADS] = nreads;
@@ -259,10 +285,10 @@ sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases
   b->hash_bytes = 2 * k <= 32 ? 4 : 8;
   b->capacity = max_bases;
   const bool staged_ok = sws::mini_staged_tile_windows(sws::SRC_DNA, k, w) > 0;  // any w: generic kernel staged
-  const uint64_t ws_bytes =
-      staged_ok ? (layout_for(b, PATH_STAGED).bytes > layout_for(b, PATH_LOOKBACK).bytes ? layout_for(b, PATH_STAGED).bytes
-                                                                                       : layout_for(b, PATH_LOOKBACK).bytes)
-                : layout_for(b, PATH_LOOKBACK).bytes;
+  const bool single_ok = sws::dna_min_fits(max_bases, k, w, mode);  // hashed k-mers, k <= 16, 4 <= w <= 17
+  uint64_t ws_bytes = layout_for(b, PATH_LOOKBACK).bytes;
+  if (staged_ok && layout_for(b, PATH_STAGED).bytes > ws_bytes) ws_bytes = layout_for(b, PATH_STAGED).bytes;
+  if (single_ok && layout_for(b, PATH_SINGLE).bytes > ws_bytes) ws_bytes = layout_for(b, PATH_SINGLE).bytes;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void **p, uint64_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
@@ -286,18 +312,22 @@ sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases
     return sws::report_error(SWS_ERR_OOM, "cannot allocate the batch buffers");
   }
   b->ws_bytes = ws_bytes;
-  const bool force_lookback = options == SWS_BATCH_LOOKBACK || !staged_ok;
-  const bool tune = options == SWS_BATCH_TUNE && staged_ok;
-  s = SWS_OK;
-  if (!force_lookback) s = capture(b, PATH_STAGED);
-  if (!s && (force_lookback || tune)) s = capture(b, PATH_LOOKBACK);
+  const bool force_lookback = options == SWS_BATCH_LOOKBACK || (!staged_ok && !single_ok);
+  const bool tune = options == SWS_BATCH_TUNE && (staged_ok || single_ok);
+  // the default: the single pass where it applies, else the staged path
+  const int first = force_lookback ? PATH_LOOKBACK : single_ok ? PATH_SINGLE : PATH_STAGED;
+  s = capture(b, first);
+  if (!s && tune) {
+    if (staged_ok && first != PATH_STAGED) s = capture(b, PATH_STAGED);
+    if (!s) s = capture(b, PATH_LOOKBACK);
+  }
   if (s) {
     free_batch(b);
     return s;
   }
-  b->path = force_lookback ? PATH_LOOKBACK : PATH_STAGED;
+  b->path = first;
   if (tune) {
-    // autotune: time both graphs on a synthetic batch of the largest size
+    // autotune: time every captured graph on a synthetic batch of the largest size
     const uint64_t len = max_bases / max_reads;
     k_fill_tune_batch<<<1024, 256, 0, b->cap>>>(b->seq, (max_bases + 3) / 4, b->offsets, max_reads,
                                                 len * max_reads);
@@ -305,13 +335,14 @@ sws_status sws_batch_create(sws_ctx *ctx, uint64_t max_reads, uint64_t max_bases
       free_batch(b);
       return err_cuda(e, "tuning batch");
     }
-    s = time_path(b, PATH_STAGED, &b->tuned_ms[PATH_STAGED]);
-    if (!s) s = time_path(b, PATH_LOOKBACK, &b->tuned_ms[PATH_LOOKBACK]);
+    for (int p = 0; p < 3 && !s; ++p)
+      if (b->exec[p]) s = time_path(b, p, &b->tuned_ms[p]);
     if (s) {
       free_batch(b);
       return s;
     }
-    b->path = b->tuned_ms[PATH_LOOKBACK] < b->tuned_ms[PATH_STAGED] ? PATH_LOOKBACK : PATH_STAGED;
+    for (int p = 0; p < 3; ++p)
+      if (b->exec[p] && b->tuned_ms[p] < b->tuned_ms[b->path]) b->path = p;
   }
   e = cudaStreamSynchronize(b->cap);
   if (e != cudaSuccess) {
@@ -339,8 +370,7 @@ sws_status sws_batch_io_get(sws_batch *b, sws_batch_io *io) {
   io->max_reads = b->max_reads;
   io->max_bases = b->max_bases;
   io->path = b->path;
-  io->tuned_ms[0] = b->tuned_ms[0];
-  io->tuned_ms[1] = b->tuned_ms[1];
+  for (int p = 0; p < 3; ++p) io->tuned_ms[p] = b->tuned_ms[p];
   return SWS_OK;
 }
 

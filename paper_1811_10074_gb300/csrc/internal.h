@@ -120,13 +120,30 @@ uint64_t keys_min_ws_bytes(uint64_t m, int w);  // workspace (zeroed by the laun
 cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *key_out, uint32_t *pos_out,
                             uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
                             cudaStream_t stream);
-// The same kernel on hashed canonical k-mers of a packed sequence (k <= 16, 4 <= w <= 17, no
-// N-blocks, the sequence 4-byte aligned): each thread hashes its 16 k-mers in registers.
-// Workspace: keys_min_ws_bytes(n - k + 1, w).
-bool dna_min_applies(const uint8_t *seq, uint64_t n, int k, int w, int mode, uint64_t n_nblocks);
-cudaError_t launch_dna_min(const uint8_t *seq, uint64_t n, int k, int w, uint32_t *key_out, uint32_t *pos_out,
-                           uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
-                           cudaStream_t stream);
+// The same kernel on hashed canonical k-mers of a packed sequence (k <= 16, 4 <= w <= 17, the
+// sequence 4-byte aligned): each thread hashes its 16 k-mers in registers.  Barriers: none,
+// N-blocks (barrier BAR_NBLOCK, nbar pairs), or the read starts of a batch (BAR_READS, nbar reads,
+// positions read-local, each read's first pick index in pick_offsets, which the caller sets to
+// all ones first and fixes up after).  With desc the sizes come from a batch descriptor and
+// n is the batch's capacity.  Workspace: dna_min_ws_bytes(n, k, w).
+struct DnaMinArgs {
+  const uint8_t *seq;
+  uint64_t n;
+  int k, w;
+  int barrier;  // -1: none
+  const int64_t *bar;
+  uint64_t nbar;
+  uint64_t *pick_offsets;
+  const unsigned long long *desc;
+  uint32_t *key_out, *pos_out;
+  uint64_t capacity;
+  uint64_t *count_out;
+};
+bool dna_min_fits(uint64_t n, int k, int w, int mode);  // the sizes and mode allow it
+bool dna_min_applies(const uint8_t *seq, uint64_t n, int k, int w, int mode);  // and seq is aligned
+int dna_min_tile_windows();
+uint64_t dna_min_ws_bytes(uint64_t n, int k, int w);
+cudaError_t launch_dna_min(const DnaMinArgs &d, void *ws, int *err, int num_sms, cudaStream_t stream);
 
 // The per-tile summary of the barriers (N-blocks or read starts) that can touch each tile.
 bool tile_barriers_needed(const MiniArgs &a, int source, int barrier);

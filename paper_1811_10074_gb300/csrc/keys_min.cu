@@ -65,6 +65,13 @@ constexpr int KCAP = 2560;                // picks a slot holds (more: the tile 
 constexpr int KSLOT_BYTES = KCAP * 8;     // (key, tile-relative position) per pick
 constexpr size_t KSMEM = 1024 + (size_t)KSTAGES * KSTAGE_STRIDE + (size_t)KSLOTS * KSLOT_BYTES;  // 2 CTAs/SM
 constexpr size_t KSMEM_DNA = 1024 + (size_t)KSLOTS * KSLOT_BYTES;  // the DNA form: pick slots only
+// Barriers of the DNA form: none, N-blocks (windows touching one are dropped), or read starts of
+// a batch (windows crossing one are dropped; positions read-local; each read's first pick noted).
+constexpr int KB_NONE = 0, KB_NBLOCK = 1, KB_READS = 2;
+constexpr int KBMAX = 128;  // barriers of a tile kept in shared memory (more: read from global)
+// read batches: a slot also keeps, per pick, the read it is the first pick of (or 0xFFFFFFFF)
+constexpr int KSLOT_BYTES_R = KCAP * 12;
+constexpr size_t KSMEM_DNA_R = 1024 + (size_t)KSLOTS * KSLOT_BYTES_R;
 constexpr uint32_t ST_DONE = 0x80000000u;  // status: count published (low bits)
 constexpr uint32_t ST_FAIL = 0xC0000000u;  // status: the tile failed
 constexpr uint32_t ST_COUNT = 0x3FFFFFFFu;
@@ -85,6 +92,13 @@ struct KeysArgs {
   const uint8_t *seq;
   uint64_t nbytes;
   uint32_t k, kmask;
+  // barriers (DNA form): N-blocks int64 [nbar][2], or read offsets int64 [nbar + 1]; per tile the
+  // first barrier that can touch it and how many (k_tile_barriers); each read's first pick index
+  const int64_t *bar;
+  uint64_t nbar;
+  const uint2 *tile_bar;
+  uint64_t *pick_offsets;
+  const unsigned long long *desc;  // a batch graph: sizes of this run (read batches)
   uint32_t m;          // keys (at most 2^32 - 2^14, so that every index below fits 32 bits)
   uint32_t n_full;     // keys in whole 32-key rows (the tensor map's extent)
   uint32_t nwin;       // windows = m - w + 1
@@ -269,11 +283,20 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
 }
 
 // Copy a placed tile's picks from its slot to the output (keys, positions): one pick per thread
-// and round, so every warp store covers 128 consecutive bytes.
+// and round, so every warp store covers 128 consecutive bytes.  A slot holds tile-relative
+// positions, or read-local ones (read batches) with, after the KCAP picks, the read each pick is
+// the first pick of; that read's pick offset is the pick's output index.
+template <int KB>
 __device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t cnt, uint32_t tile,
                                            unsigned long long base, const KeysArgs &a) {
   const uint2 *sl = reinterpret_cast<const uint2 *>(slot);
-  const uint32_t pos0 = tile * (uint32_t)KTILE;
+  const uint32_t *first = reinterpret_cast<const uint32_t *>(slot + KCAP * 8);
+  const uint32_t pos0 = KB == KB_READS ? 0u : tile * (uint32_t)KTILE;
+  if (KB == KB_READS)
+    for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
+      const uint32_t r = first[x];
+      if (r != 0xFFFFFFFFu) a.pick_offsets[r] = base + x;
+    }
   if (base + cnt <= a.capacity) {
     uint32_t *ko = a.key_out + base;
     uint32_t *po = a.pos_out + base;
@@ -294,9 +317,17 @@ __device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t c
   }
 }
 
-template <int W, bool DNA>
+template <int W, bool DNA, int KB>
 __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUtensorMap tmap, KeysArgs a) {
+  static_assert(KB == KB_NONE || DNA, "barriers belong to the DNA form");
+  constexpr int SLOTB = KB == KB_READS ? KSLOT_BYTES_R : KSLOT_BYTES;
   extern __shared__ __align__(16) unsigned char ksm_raw[];
+  // barriers of the tile of stage s in buffer s: (start, end) pairs and the index of the first and
+  // their number.  Loaded one tile ahead, read before and after the tile's barrier, rewritten two
+  // tiles later (after the next barrier).
+  __shared__ long long s_bv[KB != KB_NONE ? KSTAGES : 1][KB != KB_NONE ? 2 * KBMAX : 1];
+  __shared__ uint2 s_bt[KSTAGES];
+  __shared__ long long s_rs0[KSTAGES];  // read batches: start of the tile's first read (read g_lo)
   __shared__ __align__(8) unsigned long long s_bar[KSTAGES];
   __shared__ uint32_t s_tk[KSTAGES];
   __shared__ int s_issued[KSTAGES];  // a copy was issued into the stage and not yet waited for
@@ -308,8 +339,35 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   unsigned char *stages = ksm_raw + ((1024u - (tma::smem_u32(ksm_raw) & 1023u)) & 1023u);
   unsigned char *slots = stages + (DNA ? 0 : KSTAGES * KSTAGE_STRIDE);  // the DNA form stages nothing
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (KB == KB_READS && a.desc) {  // a batch graph: this run's sizes
+    const uint64_t n = a.desc[BD_TOTAL];
+    const uint64_t m = n >= a.k ? n - a.k + 1 : 0;
+    a.m = (uint32_t)m;
+    a.nwin = (uint32_t)a.desc[BD_NWIN];
+    a.num_tiles = (uint32_t)a.desc[BD_TILES];
+    a.nbytes = (n + 3) / 4;
+    a.nbar = a.desc[BD_NREADS];
+  }
   const uint32_t T = a.num_tiles;
   constexpr uint32_t NONE = 0xFFFFFFFFu;
+  // barrier i of the list: an N-block [start, end), or a read start (start = end), read i + 1
+  auto gstart = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i] : a.bar[i + 1]; };
+  auto gend = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i + 1] : a.bar[i + 1]; };
+  // all threads: tile `tile`'s barriers into buffer `buf` (a tile with more than KBMAX keeps its
+  // list in global memory)
+  auto load_bars = [&](uint32_t tile, int buf) {
+    if (KB == KB_NONE || tile >= T) return;
+    const uint2 tbr = a.tile_bar[tile];
+    if (t == 0) {
+      s_bt[buf] = tbr;
+      if (KB == KB_READS) s_rs0[buf] = a.bar[tbr.x];
+    }
+    if (tbr.y <= (uint32_t)KBMAX)
+      for (uint32_t i = t; i < tbr.y; i += KNT) {
+        s_bv[buf][2 * i] = gstart(tbr.x + i);
+        s_bv[buf][2 * i + 1] = gend(tbr.x + i);
+      }
+  };
 
   auto issue = [&](int s, uint32_t tile) {  // thread 0: rows 128 tile - 1 .. 128 tile + 128
     tma::mbar_arrive_expect_tx(&s_bar[s], KSTAGE_BYTES);
@@ -342,6 +400,10 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   const uint32_t first_dyn = (uint32_t)KSTAGES * gridDim.x;  // the first ticket handed out dynamically
   uint32_t spare = t == 0 ? first_dyn + atomicAdd(&a.hdr->ticket, 1u) : 0u;
   __syncthreads();
+  if (KB != KB_NONE) {
+    load_bars(s_tk[0], 0);
+    __syncthreads();
+  }
 
   uint32_t phases = 0;             // bit s: parity of stage s's next completion
   int run_tile = -1;               // the last tile whose picks were placed ...
@@ -363,6 +425,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     const int s = it % KSTAGES, par = it & 1;
     const uint32_t tile = s_tk[s];
     if (tile >= T) break;
+    // the next tile's barriers, visible after this tile's barrier (its ticket was written at least
+    // one barrier ago; its buffer was last read two tiles ago, before the previous tile's barrier)
+    if (KB != KB_NONE) load_bars(s_tk[(it + 1) % KSTAGES], (it + 1) % KSTAGES);
     // ---- this tile's keys (each thread waits for the copy itself) ---------------------------------
     const bool issued = !DNA && s_issued[s] != 0 && !failed;  // a failed CTA waits for its copies at exit
     // the counts before the oldest deferred tile (placed after this tile's barrier): two status
@@ -378,7 +443,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     const uint32_t g0 = tb + (uint32_t)q0;      // this thread's first window
     uint32_t mv[KWPT];
     int mp[KWPT];
-    unsigned mask = 0;  // windows that store a pick
+    unsigned mask = 0;      // windows that store a pick
+    unsigned firstm = 0;    // barriers: stored picks that open an N-free stretch or a read
+    uint32_t qstart = 0;    // barriers: the first one (in the tile's list) ending after g0 - 1
     if (wok) {
       uint32_t X[32];
       uint32_t xm1;
@@ -474,6 +541,45 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       const int left = (int)(a.nwin - g0);  // windows of this thread inside the sequence (if > 0)
       if (g0 >= a.nwin) mask = 0;
       else if (left < KWPT) mask &= (1u << left) - 1u;
+      if constexpr (KB != KB_NONE) {
+        // a window touching a barrier is dropped; the first window after a dropped one always
+        // stores its pick (a new N-free stretch, or a new read)
+        const uint2 tbr = s_bt[s];
+        const uint32_t nb = tbr.y;
+        const bool in_smem = nb <= (uint32_t)KBMAX;
+        auto bst = [&](uint32_t i) -> long long { return in_smem ? s_bv[s][2 * i] : gstart(tbr.x + i); };
+        auto ben = [&](uint32_t i) -> long long { return in_smem ? s_bv[s][2 * i + 1] : gend(tbr.x + i); };
+        const long long span = (long long)W + a.k - 1;
+        const long long pf = (long long)g0 - 1;
+        uint32_t q = 0, hi = nb;
+        while (q < hi) {
+          const uint32_t mid = (q + hi) >> 1;
+          if (ben(mid) > pf) hi = mid;
+          else q = mid + 1;
+        }
+        qstart = q;
+        // windows g0 - 1 .. g0 + 15 as bits 0 .. 16: barrier [bs, be) drops the windows
+        // [bs - span + 1, be - 1]; the barriers from q on, while they reach this thread's windows
+        unsigned v17 = (2u << KWPT) - 1u;
+        for (uint32_t qq = q; qq < nb; ++qq) {
+          const long long bs = bst(qq);
+          if (bs - span + 1 > (long long)g0 + KWPT - 1) break;  // it and every later one start beyond
+          const long long lo = bs - span + 1 - pf, hi2 = ben(qq) - 1 - pf;
+          if (hi2 >= 0) {
+            const int l = lo < 0 ? 0 : (int)lo, h = hi2 > KWPT ? KWPT : (int)hi2;
+            v17 &= ~(((2u << h) - 1u) & ~((1u << l) - 1u));
+          }
+        }
+        const long long lim = (long long)a.nwin - pf;  // bits of windows past the last are dropped
+        if (lim <= 0) v17 = 0;
+        else if (lim <= KWPT) v17 &= (1u << lim) - 1u;
+        if (g0 == 0) v17 &= ~1u;  // no window before the first
+        const unsigned vmask = v17 >> 1;
+        const bool pvalid = v17 & 1u;
+        const unsigned prevv = ((vmask << 1) | (pvalid ? 1u : 0u)) & ((1u << KWPT) - 1u);
+        firstm = vmask & ~prevv;
+        mask = (mask | firstm) & vmask;
+      }
     }
     const uint32_t cnt = __popc(mask);
     uint32_t inc = cnt;
@@ -533,7 +639,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     //      every tile in between (published two tiles ago or earlier) ----------------------------------
     if (pop) {
       const unsigned long long base = run_end + between;
-      write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
+      write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
       if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
       run_tile = pt0;
       run_end = base + pc0;
@@ -546,12 +652,32 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       // ---- defer this tile: its picks wait in the next slot -----------------------------------------
       const int sl = (int)(pushes % KSLOTS);
       ++pushes;
-      uint2 *dst = reinterpret_cast<uint2 *>(slots + sl * KSLOT_BYTES) + (woff + inc - cnt);
+      uint2 *dst = reinterpret_cast<uint2 *>(slots + sl * SLOTB) + (woff + inc - cnt);
+      if constexpr (KB == KB_READS) {
+        // read-local positions, and the read whose first pick it is
+        uint32_t *fst = reinterpret_cast<uint32_t *>(slots + sl * SLOTB + KCAP * 8) + (woff + inc - cnt);
+        const uint2 tbr = s_bt[s];
+        const bool in_smem = tbr.y <= (uint32_t)KBMAX;
+        uint32_t qq = qstart;
 #pragma unroll
-      for (int j = 0; j < KWPT; ++j) {
-        if ((mask >> j) & 1u) {
-          *dst = make_uint2(mv[j], (uint32_t)(q0 + mp[j]));
-          ++dst;
+        for (int j = 0; j < KWPT; ++j) {
+          if ((mask >> j) & 1u) {
+            while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
+            const uint32_t rd = tbr.x + qq;  // read g_lo + qq starts where barrier qq - 1 is
+            const long long rs = qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1));
+            *dst = make_uint2(mv[j], tb + (uint32_t)(q0 + mp[j]) - (uint32_t)rs);
+            *fst = (firstm >> j) & 1u ? rd : NONE;
+            ++dst;
+            ++fst;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KWPT; ++j) {
+          if ((mask >> j) & 1u) {
+            *dst = make_uint2(mv[j], (uint32_t)(q0 + mp[j]));
+            ++dst;
+          }
         }
       }
       if (L == 0) {
@@ -575,7 +701,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           break;
         }
         const unsigned long long base = run_end + btw;
-        write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
+        write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
         if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
         run_tile = pt0;
         run_end = base + pc0;
@@ -592,12 +718,22 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         } else {
           const unsigned long long base = run_end + btw;
           unsigned long long r = base + woff + inc - cnt;
+          const uint2 tbr = KB == KB_READS ? s_bt[s] : make_uint2(0u, 0u);
+          uint32_t qq = qstart;
 #pragma unroll
           for (int j = 0; j < KWPT; ++j) {
             if ((mask >> j) & 1u) {
+              uint32_t pos = tb + (uint32_t)(q0 + mp[j]);
+              if (KB == KB_READS) {
+                const bool in_smem = tbr.y <= (uint32_t)KBMAX;
+                while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
+                const uint32_t rd = tbr.x + qq;
+                pos -= (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+                if ((firstm >> j) & 1u) a.pick_offsets[rd] = r;
+              }
               if (r < a.capacity) {
                 a.key_out[r] = mv[j];
-                a.pos_out[r] = tb + (uint32_t)(q0 + mp[j]);
+                a.pos_out[r] = pos;
               }
               ++r;
             }
@@ -618,7 +754,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       break;
     }
     const unsigned long long base = run_end + btw;
-    write_slot(slots + ps0 * KSLOT_BYTES, pc0, pt0, base, a);
+    write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
     if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
     run_tile = pt0;
     run_end = base + pc0;
@@ -659,10 +795,10 @@ EncodeTiledK encode_tiled_k() {
   return fn;
 }
 
-template <int W, bool DNA>
+template <int W, bool DNA, int KB>
 cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms, cudaStream_t st) {
-  auto kern = k_keys_min<W, DNA>;
-  constexpr size_t smem = DNA ? KSMEM_DNA : KSMEM;
+  auto kern = k_keys_min<W, DNA, KB>;
+  constexpr size_t smem = !DNA ? KSMEM : KB == KB_READS ? KSMEM_DNA_R : KSMEM_DNA;
   static int per_sm[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -684,56 +820,98 @@ cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms
 
 }  // namespace
 
-bool dna_min_applies(const uint8_t *seq, uint64_t n, int k, int w, int mode, uint64_t n_nblocks) {
-  if (mode != SWS_MINI_HASH || k < 1 || k > 16 || w < 4 || w > KMAXW || n_nblocks != 0) return false;
-  if ((reinterpret_cast<uintptr_t>(seq) & 3u) != 0 || n < (uint64_t)k + 32) return false;
+bool dna_min_fits(uint64_t n, int k, int w, int mode) {
+  if (mode != SWS_MINI_HASH || k < 1 || k > 16 || w < 4 || w > KMAXW || n < (uint64_t)k + 32) return false;
   const uint64_t m = n - (uint64_t)k + 1;
   return m <= (1ull << 32) - (1ull << 14) && (uint64_t)w <= m;
 }
 
-cudaError_t launch_dna_min(const uint8_t *seq, uint64_t n, int k, int w, uint32_t *key_out, uint32_t *pos_out,
-                           uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
-                           cudaStream_t st) {
-  if (!dna_min_applies(seq, n, k, w, SWS_MINI_HASH, 0)) return cudaErrorInvalidValue;
-  const uint64_t m = n - (uint64_t)k + 1;  // k-mers: the keys
-  const uint64_t nwin = m - (uint64_t)w + 1;
-  const uint64_t tiles = (nwin + KTILE - 1) / KTILE;
-  cudaError_t e = cudaMemsetAsync(ws, 0, keys_min_ws_bytes(m, w), st);
+bool dna_min_applies(const uint8_t *seq, uint64_t n, int k, int w, int mode) {
+  return (reinterpret_cast<uintptr_t>(seq) & 3u) == 0 && dna_min_fits(n, k, w, mode);
+}
+
+int dna_min_tile_windows() { return KTILE; }
+
+static uint64_t dna_tiles(uint64_t n, int k, int w) {
+  const uint64_t m = n - (uint64_t)k + 1;
+  return (m - (uint64_t)w + KTILE) / KTILE;  // ceil(nwin / KTILE), nwin = m - w + 1
+}
+
+uint64_t dna_min_ws_bytes(uint64_t n, int k, int w) {
+  const uint64_t m = n - (uint64_t)k + 1;
+  return (keys_min_ws_bytes(m, w) + 255) / 256 * 256 + dna_tiles(n, k, w) * sizeof(uint2);
+}
+
+template <int KB>
+static cudaError_t launch_dna_kb(const KeysArgs &a, int w, int num_sms, cudaStream_t st) {
+  CUtensorMap none{};  // the DNA form has no tensor map
+  switch (w) {
+    case 4: return launch_w_keys<4, true, KB>(none, a, num_sms, st);
+    case 5: return launch_w_keys<5, true, KB>(none, a, num_sms, st);
+    case 6: return launch_w_keys<6, true, KB>(none, a, num_sms, st);
+    case 7: return launch_w_keys<7, true, KB>(none, a, num_sms, st);
+    case 8: return launch_w_keys<8, true, KB>(none, a, num_sms, st);
+    case 9: return launch_w_keys<9, true, KB>(none, a, num_sms, st);
+    case 10: return launch_w_keys<10, true, KB>(none, a, num_sms, st);
+    case 11: return launch_w_keys<11, true, KB>(none, a, num_sms, st);
+    case 12: return launch_w_keys<12, true, KB>(none, a, num_sms, st);
+    case 13: return launch_w_keys<13, true, KB>(none, a, num_sms, st);
+    case 14: return launch_w_keys<14, true, KB>(none, a, num_sms, st);
+    case 15: return launch_w_keys<15, true, KB>(none, a, num_sms, st);
+    case 16: return launch_w_keys<16, true, KB>(none, a, num_sms, st);
+    case 17: return launch_w_keys<17, true, KB>(none, a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_dna_min(const DnaMinArgs &d, void *ws, int *err, int num_sms, cudaStream_t st) {
+  if (!dna_min_applies(d.seq, d.n, d.k, d.w, SWS_MINI_HASH)) return cudaErrorInvalidValue;
+  const uint64_t m = d.n - (uint64_t)d.k + 1;  // k-mers: the keys
+  const uint64_t nwin = m - (uint64_t)d.w + 1;
+  const uint64_t tiles = dna_tiles(d.n, d.k, d.w);
+  cudaError_t e = cudaMemsetAsync(ws, 0, keys_min_ws_bytes(m, d.w), st);
   if (e != cudaSuccess) return e;
   KeysArgs a{};
-  a.seq = seq;
-  a.nbytes = (n + 3) / 4;
-  a.k = (uint32_t)k;
-  a.kmask = 0xFFFFFFFFu >> (32 - 2 * k);
+  a.seq = d.seq;
+  a.nbytes = (d.n + 3) / 4;
+  a.k = (uint32_t)d.k;
+  a.kmask = 0xFFFFFFFFu >> (32 - 2 * d.k);
   a.m = (uint32_t)m;
   a.n_full = (uint32_t)m;
   a.nwin = (uint32_t)nwin;
   a.num_tiles = (uint32_t)tiles;
   a.hdr = static_cast<KeysHeader *>(ws);
   a.status = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
-  a.key_out = key_out;
-  a.pos_out = pos_out;
-  a.capacity = capacity;
-  a.count_out = count_out;
+  a.key_out = d.key_out;
+  a.pos_out = d.pos_out;
+  a.capacity = d.capacity;
+  a.count_out = d.count_out;
   a.err = err;
-  CUtensorMap none{};  // the DNA form has no tensor map
-  switch (w) {
-    case 4: return launch_w_keys<4, true>(none, a, num_sms, st);
-    case 5: return launch_w_keys<5, true>(none, a, num_sms, st);
-    case 6: return launch_w_keys<6, true>(none, a, num_sms, st);
-    case 7: return launch_w_keys<7, true>(none, a, num_sms, st);
-    case 8: return launch_w_keys<8, true>(none, a, num_sms, st);
-    case 9: return launch_w_keys<9, true>(none, a, num_sms, st);
-    case 10: return launch_w_keys<10, true>(none, a, num_sms, st);
-    case 11: return launch_w_keys<11, true>(none, a, num_sms, st);
-    case 12: return launch_w_keys<12, true>(none, a, num_sms, st);
-    case 13: return launch_w_keys<13, true>(none, a, num_sms, st);
-    case 14: return launch_w_keys<14, true>(none, a, num_sms, st);
-    case 15: return launch_w_keys<15, true>(none, a, num_sms, st);
-    case 16: return launch_w_keys<16, true>(none, a, num_sms, st);
-    case 17: return launch_w_keys<17, true>(none, a, num_sms, st);
-    default: return cudaErrorInvalidValue;
+  a.bar = d.bar;
+  a.nbar = d.nbar;
+  a.pick_offsets = d.pick_offsets;
+  a.desc = d.desc;
+  int kb = KB_NONE;
+  if (d.barrier == BAR_NBLOCK && d.nbar > 0) kb = KB_NBLOCK;
+  if (d.barrier == BAR_READS) kb = KB_READS;
+  if (kb != KB_NONE) {
+    // per tile the barriers that can touch its windows (tiles of KTILE windows)
+    uint2 *tile_bar = reinterpret_cast<uint2 *>(static_cast<char *>(ws) + (keys_min_ws_bytes(m, d.w) + 255) / 256 * 256);
+    MiniArgs ma{};
+    ma.bar = d.bar;
+    ma.nbar = d.nbar;
+    ma.tile_bar = tile_bar;
+    ma.desc = d.desc;
+    if (tile_barriers_needed(ma, SRC_DNA, d.barrier))
+      e = launch_tile_barriers(ma, SRC_DNA, d.barrier, tiles, KTILE, d.w + d.k - 1, st);
+    else  // one read: no barrier between its windows
+      e = cudaMemsetAsync(tile_bar, 0, tiles * sizeof(uint2), st);
+    if (e != cudaSuccess) return e;
+    a.tile_bar = tile_bar;
   }
+  if (kb == KB_NBLOCK) return launch_dna_kb<KB_NBLOCK>(a, d.w, num_sms, st);
+  if (kb == KB_READS) return launch_dna_kb<KB_READS>(a, d.w, num_sms, st);
+  return launch_dna_kb<KB_NONE>(a, d.w, num_sms, st);
 }
 
 bool keys_min_applies(const uint32_t *keys, uint64_t m, int w) {
@@ -778,23 +956,23 @@ cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *k
   a.count_out = count_out;
   a.err = err;
   switch (w) {
-    case 1: return launch_w_keys<1, false>(map, a, num_sms, st);
-    case 2: return launch_w_keys<2, false>(map, a, num_sms, st);
-    case 3: return launch_w_keys<3, false>(map, a, num_sms, st);
-    case 4: return launch_w_keys<4, false>(map, a, num_sms, st);
-    case 5: return launch_w_keys<5, false>(map, a, num_sms, st);
-    case 6: return launch_w_keys<6, false>(map, a, num_sms, st);
-    case 7: return launch_w_keys<7, false>(map, a, num_sms, st);
-    case 8: return launch_w_keys<8, false>(map, a, num_sms, st);
-    case 9: return launch_w_keys<9, false>(map, a, num_sms, st);
-    case 10: return launch_w_keys<10, false>(map, a, num_sms, st);
-    case 11: return launch_w_keys<11, false>(map, a, num_sms, st);
-    case 12: return launch_w_keys<12, false>(map, a, num_sms, st);
-    case 13: return launch_w_keys<13, false>(map, a, num_sms, st);
-    case 14: return launch_w_keys<14, false>(map, a, num_sms, st);
-    case 15: return launch_w_keys<15, false>(map, a, num_sms, st);
-    case 16: return launch_w_keys<16, false>(map, a, num_sms, st);
-    case 17: return launch_w_keys<17, false>(map, a, num_sms, st);
+    case 1: return launch_w_keys<1, false, KB_NONE>(map, a, num_sms, st);
+    case 2: return launch_w_keys<2, false, KB_NONE>(map, a, num_sms, st);
+    case 3: return launch_w_keys<3, false, KB_NONE>(map, a, num_sms, st);
+    case 4: return launch_w_keys<4, false, KB_NONE>(map, a, num_sms, st);
+    case 5: return launch_w_keys<5, false, KB_NONE>(map, a, num_sms, st);
+    case 6: return launch_w_keys<6, false, KB_NONE>(map, a, num_sms, st);
+    case 7: return launch_w_keys<7, false, KB_NONE>(map, a, num_sms, st);
+    case 8: return launch_w_keys<8, false, KB_NONE>(map, a, num_sms, st);
+    case 9: return launch_w_keys<9, false, KB_NONE>(map, a, num_sms, st);
+    case 10: return launch_w_keys<10, false, KB_NONE>(map, a, num_sms, st);
+    case 11: return launch_w_keys<11, false, KB_NONE>(map, a, num_sms, st);
+    case 12: return launch_w_keys<12, false, KB_NONE>(map, a, num_sms, st);
+    case 13: return launch_w_keys<13, false, KB_NONE>(map, a, num_sms, st);
+    case 14: return launch_w_keys<14, false, KB_NONE>(map, a, num_sms, st);
+    case 15: return launch_w_keys<15, false, KB_NONE>(map, a, num_sms, st);
+    case 16: return launch_w_keys<16, false, KB_NONE>(map, a, num_sms, st);
+    case 17: return launch_w_keys<17, false, KB_NONE>(map, a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,9 +40,9 @@ def check_run(bt, seq, offs, k, w, mode="hash"):
 def test_batch_graph_replays_any_size(options):
     rng = np.random.default_rng({"default": 1, "lookback": 2, "tune": 3}[options])
     bt = B.Batch(max_reads=3000, max_bases=600_000, k=15, w=10, options=options)
-    if options == "tune":
-        assert all(t > 0 for t in bt.tuned_ms) and bt.path in (0, 1)
-    assert bt.path == {"default": 0, "lookback": 1}.get(options, bt.path)
+    if options == "tune":  # all three paths timed: staged, look-back, single pass
+        assert all(t > 0 for t in bt.tuned_ms) and bt.path in (0, 1, 2)
+    assert bt.path == {"default": 2, "lookback": 1}.get(options, bt.path)
     batches = [make_batch(rng, 2000, 100, 250, 11), make_batch(rng, 30, 1000, 20000, 12),
                make_batch(rng, 3000, 0, 30, 13), make_batch(rng, 1, 50, 50, 14), make_batch(rng, 2999, 150, 199, 15)]
     for seq, offs in batches:
@@ -66,6 +66,20 @@ def test_batch_wide_keys(options):
     for i in range(2):
         seq, offs = make_batch(rng, 400, 60, 400, 20 + i)
         check_run(bt, seq, offs, 19, 10)
+    bt.close()
+
+
+@pytest.mark.parametrize("k,w", [(16, 17), (5, 4)])
+def test_batch_single_pass_graph(k, w):
+    """The default graph for hashed k-mers with k <= 16 and 4 <= w <= 17 is the single pass, the
+    sizes read from the device descriptor at every replay."""
+    rng = np.random.default_rng(k + w)
+    bt = B.Batch(max_reads=4000, max_bases=400_000, k=k, w=w)
+    assert bt.path == 2
+    for lo, hi, nreads in ((100, 250, 1500), (0, 3 * (k + w), 4000), (20_000, 90_000, 4), (k + 40, k + 40, 1)):
+        seq, offs = make_batch(rng, nreads, lo, hi, int(rng.integers(1 << 30)))
+        if offs[-1] <= 400_000:
+            check_run(bt, seq, offs, k, w)
     bt.close()
 
 

@@ -342,3 +342,50 @@ def test_dna_single_pass_kernel(w):
     h, p = B.minimizers(fd[1:], n, 15, w)
     rh, rp = oracle.minimizers(full[1:].clone(), n, 15, w)
     assert (to_u64(h) == rh).all() and (p.cpu().numpy().view(np.uint32) == rp).all()
+
+
+def check_batch_single_pass(seq, offs, k, w):
+    total = int(offs[-1])
+    h, p, po = B.minimizers_batch(seq.cuda(), torch.from_numpy(offs).cuda(), total, k, w, "hash")
+    rh, rp, rpo = oracle.minimizers_batch(seq, offs, k, w, "hash")
+    assert (po.cpu().numpy().view(np.uint64) == rpo).all(), (k, w, offs.size)
+    gh, gp = to_u64(h), p.cpu().numpy().view(np.uint32)
+    assert gh.shape == rh.shape, (k, w, gh.shape, rh.shape)
+    bad = np.nonzero((gh != rh) | (gp != rp))[0]
+    assert bad.size == 0, (k, w, bad[:5], gp[bad[:5]], rp[bad[:5]])
+
+
+# Read batches on the single-pass kernel (hashed k-mers, k <= 16, 4 <= w <= 17): read starts act
+# as window barriers, positions are read-local, each read's first pick gives its pick offset.
+@pytest.mark.parametrize("k,w", [(15, 10), (16, 17), (5, 4), (11, 13)])
+def test_batch_single_pass_kernel(k, w):
+    rng = np.random.default_rng(k * 100 + w)
+    span = k + w - 1
+    cases = [
+        rng.integers(100, 251, size=3000),                      # short reads
+        rng.integers(0, 3 * span, size=4000),                   # tiny and empty reads: > 128 starts a tile
+        np.array([4096 * 3 + span - 1]),                        # one read, 3 tiles exactly
+        np.array([span - 1, span, span + 1, 0, 5000, 1, 4095 + span, 4097]),
+        rng.integers(5_000, 60_000, size=40),                   # long reads across tiles
+    ]
+    for lens in cases:
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        if offs[-1] < k + 32:
+            continue
+        seq = synth.acgt_uniform_packed(int(offs[-1]), seed=int(rng.integers(1 << 30)))
+        check_batch_single_pass(seq, offs, k, w)
+    # low complexity: ties inside reads and across read starts
+    lens = rng.integers(20, 400, size=2000)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    codes = np.tile(np.array([0, 0, 1, 0, 0, 1, 2], np.uint8), int(offs[-1]) // 7 + 1)[: int(offs[-1])]
+    check_batch_single_pass(synth.pack_codes(torch.from_numpy(codes)), offs, k, w)
+
+
+# The same kernel with N-blocks (windows touching one dropped, the first window after one stores).
+@pytest.mark.parametrize("w", [4, 10, 17])
+def test_nblocks_single_pass_kernel(w):
+    rng = np.random.default_rng(500 + w)
+    for n, count, maxlen in ((300_000, 3000, 30), (200_000, 50, 20_000), (100_000, 600, 3)):
+        seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
+        iv = random_nblocks(n, rng, count, maxlen)
+        check_minimizers(seq, n, 15, w, "hash", iv)
