@@ -486,23 +486,24 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         }
       }
       window_minima<W>(X, mv, mp);
-      // the pick of the window before this thread's first: the previous lane's last, shifted to
-      // this thread's frame; lane 0 of each warp finds it from its own keys
-      // A window stores a pick when its pick differs from the previous window's pick: when its
-      // least key differs from the previous window's, or equals it but the previous window's pick
-      // was its first key (which has left).  Values decide it; the window before this thread's
-      // first is the previous lane's last (lane 0 of each warp computes it).
-      uint32_t pm = __shfl_up_sync(kFull, mv[KWPT - 1], 1);
-      uint32_t px = __shfl_up_sync(kFull, X[KWPT - 1], 1);
+      // A window stores a pick when its pick (the position of its leftmost least key) differs
+      // from the previous window's.  The window before this thread's first is the previous lane's
+      // last (its position shifted to this thread's frame); lane 0 of each warp finds it from its
+      // own keys: the k-mer before its first (position -1) and its first w - 1.
+      int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
       if (lane == 0) {
-        pm = xm1;
+        uint32_t best = xm1;
+        pp = -1;
 #pragma unroll
-        for (int i = 0; i < W - 1; ++i) pm = min(pm, X[i]);
-        px = xm1;
+        for (int i = 0; i < W - 1; ++i)
+          if (X[i] < best) {
+            best = X[i];
+            pp = i;
+          }
       }
-      mask = (mv[0] != pm || px == pm || g0 == 0) ? 1u : 0u;
+      mask = (mp[0] != pp || g0 == 0) ? 1u : 0u;
 #pragma unroll
-      for (int j = 1; j < KWPT; ++j) mask |= (unsigned)(mv[j] != mv[j - 1] || X[j - 1] == mv[j - 1]) << j;
+      for (int j = 1; j < KWPT; ++j) mask |= (unsigned)(mp[j] != mp[j - 1]) << j;
       const int left = (int)(a.nwin - g0);  // windows of this thread inside the sequence (if > 0)
       if (g0 >= a.nwin) mask = 0;
       else if (left < KWPT) mask &= (1u << left) - 1u;
