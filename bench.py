@@ -785,24 +785,27 @@ def serve_extras(ctx, n_requests: int = 3000, duration_s: float = 1.5, p99_bound
                 "batches": int(st["batches"]),
                 "client_late_p99_ms": round(float(np.percentile(late, 99)) * 1e3, 3)}
 
-    # capacity: the highest offered rate (Poisson arrivals, rates growing by 1.15x) that is still
-    # served, i.e. answered at >= 97% of the offered rate with p99 within p99_bound_ms; the ladder
-    # stops one step past it
-    ladder, cap, g, step = [], 0.0, 8.0, 0
-    while step < 16:
+    # capacity: the highest offered rate (Poisson arrivals, rates growing by 1.15x) that is served,
+    # i.e. answered at >= 97% of the offered rate with p99 within p99_bound_ms.  The ladder goes on
+    # past a step whose p99 alone misses (a stall of the client or the host can do that once) and
+    # stops after two steps in a row that are not answered at the offered rate.
+    ladder, cap, g, step, short = [], 0.0, 8.0, 0, 0
+    while step < 16 and short < 2:
         r = load(g, 100 + step)
-        ok = r["gbp_s"] >= 0.97 * g and r["p99_ms"] <= p99_bound_ms
+        kept_up = r["gbp_s"] >= 0.97 * g
+        ok = kept_up and r["p99_ms"] <= p99_bound_ms
         ladder.append(dict(r, sustained=ok))
-        if not ok:
-            break
-        cap = r["gbp_s"]
+        short = 0 if kept_up else short + 1
+        if ok:
+            cap = max(cap, r["gbp_s"])
         g *= 1.15
         step += 1
     out = {"workload": "requests log-uniform 150 bp - 1 Mbp, uniform ACGT, k=15 w=10; 4 slots, <=128 requests "
                        "and <=16 Mbp per batch; answers collected in place and released by a client thread",
            "capacity_gbp_s": round(cap, 3),
            "capacity_definition": f"highest offered rate of a ladder of Poisson loads (x1.15 steps from 8 Gbp/s, "
-                                  f"{duration_s} s each) answered at >= 97% of it with p99 <= {p99_bound_ms} ms",
+                                  f"{duration_s} s each, until two steps in a row fall short) answered at >= 97% "
+                                  f"of it with p99 <= {p99_bound_ms} ms",
            "loads": []}
     for r in ladder:
         out["loads"].append(dict(r, offered_x_capacity=round(r["offered_gbp_s"] / cap, 3) if cap else None))

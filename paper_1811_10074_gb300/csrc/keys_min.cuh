@@ -411,6 +411,11 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     unsigned mask = 0;      // windows that store a pick
     unsigned firstm = 0;    // barriers: stored picks that open an N-free stretch or a read
     uint32_t qstart = 0;    // barriers: the first one (in the tile's list) ending after g0 - 1
+    // read batches: window g0 + j lies in read g_lo + qstart + (j >= d1) + (j >= d2), which starts
+    // at r0, c1 or c2 (unless more than two reads start among the windows: many)
+    int d1 = KWPT, d2 = KWPT;
+    uint32_t r0 = 0, c1 = 0, c2 = 0;
+    bool many = false;
     if (wok) {
       uint32_t X[32];
       uint32_t xm1;
@@ -524,6 +529,18 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           else q = mid + 1;
         }
         qstart = q;
+        if constexpr (KB == KB_READS) {
+          r0 = (uint32_t)(q == 0 ? s_rs0[s] : bst(q - 1));
+          if (q < nb) {
+            c1 = (uint32_t)bst(q);
+            d1 = c1 - g0 < (uint32_t)KWPT ? (int)(c1 - g0) : KWPT;
+          }
+          if (q + 1 < nb) {
+            c2 = (uint32_t)bst(q + 1);
+            d2 = c2 - g0 < (uint32_t)KWPT ? (int)(c2 - g0) : KWPT;
+          }
+          many = q + 2 < nb && bst(q + 2) - (long long)g0 < KWPT;
+        }
         // windows g0 - 1 .. g0 + 15 as bits 0 .. 16: barrier [bs, be) drops the windows
         // [bs - span + 1, be - 1]; the barriers from q on, while they reach this thread's windows
         unsigned v17 = (2u << KWPT) - 1u;
@@ -628,10 +645,17 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
 #pragma unroll
         for (int j = 0; j < KWPT; ++j) {
           if ((mask >> j) & 1u) {
-            while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
-            const uint32_t rd = tbr.x + qq;  // read g_lo + qq starts where barrier qq - 1 is
-            const long long rs = qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1));
-            *dst = make_uint2(mv[j], tb + (uint32_t)(q0 + mp[j]) - (uint32_t)rs);
+            uint32_t rd, rs;
+            if (!many) {
+              const int i = (j >= d1) + (j >= d2);
+              rd = tbr.x + qstart + (uint32_t)i;
+              rs = i == 0 ? r0 : i == 1 ? c1 : c2;
+            } else {
+              while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
+              rd = tbr.x + qq;  // read g_lo + qq starts where barrier qq - 1 is
+              rs = (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+            }
+            *dst = make_uint2(mv[j], tb + (uint32_t)(q0 + mp[j]) - rs);
             *fst = (firstm >> j) & 1u ? rd : NONE;
             ++dst;
             ++fst;
@@ -692,9 +716,16 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
               uint32_t pos = tb + (uint32_t)(q0 + mp[j]);
               if (KB == KB_READS) {
                 const bool in_smem = tbr.y <= (uint32_t)KBMAX;
-                while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
-                const uint32_t rd = tbr.x + qq;
-                pos -= (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+                uint32_t rd;
+                if (!many) {
+                  const int i = (j >= d1) + (j >= d2);
+                  rd = tbr.x + qstart + (uint32_t)i;
+                  pos -= i == 0 ? r0 : i == 1 ? c1 : c2;
+                } else {
+                  while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
+                  rd = tbr.x + qq;
+                  pos -= (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+                }
                 if ((firstm >> j) & 1u) a.pick_offsets[rd] = r;
               }
               if (r < a.capacity) {
