@@ -481,6 +481,7 @@ static sws_status minimizers_common(sws_ctx *ctx, int source, const uint8_t *seq
     d.bar = nblocks;
     d.nbar = n_nblocks;
     d.key_out = static_cast<uint32_t *>(hash_out);
+    d.key_out64 = static_cast<unsigned long long *>(hash_out);
     d.pos_out = pos_out;
     d.capacity = capacity;
     d.count_out = count_out;
@@ -645,6 +646,7 @@ sws_status sws_minimizers_batch(sws_ctx *ctx, const uint8_t *seq, const int64_t 
     d.nbar = nreads;
     d.pick_offsets = pick_offsets;
     d.key_out = static_cast<uint32_t *>(hash_out);
+    d.key_out64 = static_cast<unsigned long long *>(hash_out);
     d.pos_out = pos_out;
     d.capacity = capacity;
     d.count_out = count_out;

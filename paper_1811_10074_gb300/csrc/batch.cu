@@ -141,6 +141,7 @@ sws_status enqueue(sws_batch *b, int path, cudaStream_t st) {
     d.pick_offsets = b->pick_offsets;
     d.desc = b->d_desc;
     d.key_out = static_cast<uint32_t *>(b->hash);
+    d.key_out64 = static_cast<unsigned long long *>(b->hash);
     d.pos_out = b->pos;
     d.capacity = b->capacity;
     d.count_out = b->count;

@@ -120,8 +120,9 @@ uint64_t keys_min_ws_bytes(uint64_t m, int w);  // workspace (zeroed by the laun
 cudaError_t launch_keys_min(const uint32_t *keys, uint64_t m, int w, uint32_t *key_out, uint32_t *pos_out,
                             uint64_t capacity, uint64_t *count_out, void *ws, int *err, int num_sms,
                             cudaStream_t stream);
-// The same kernel on hashed canonical k-mers of a packed sequence (k <= 16, 4 <= w <= 17, the
-// sequence 4-byte aligned): each thread hashes its 16 k-mers in registers.  Barriers: none,
+// The same kernel on hashed canonical k-mers of a packed sequence (k <= 29, 4 <= w <= 17, the
+// sequence 4-byte aligned; 64-bit keys above k = 16): each thread hashes its 16 k-mers in
+// registers.  Barriers: none,
 // N-blocks (barrier BAR_NBLOCK, nbar pairs), or the read starts of a batch (BAR_READS, nbar reads,
 // positions read-local, each read's first pick index in pick_offsets, which the caller sets to
 // all ones first and fixes up after).  With desc the sizes come from a batch descriptor and
@@ -136,6 +137,7 @@ struct DnaMinArgs {
   uint64_t *pick_offsets;
   const unsigned long long *desc;
   uint32_t *key_out, *pos_out;
+  unsigned long long *key_out64;  // the keys when k > 16
   uint64_t capacity;
   uint64_t *count_out;
 };

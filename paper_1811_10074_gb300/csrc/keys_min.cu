@@ -70,7 +70,7 @@ EncodeTiledK encode_tiled_k() {
 
 
 bool dna_min_fits(uint64_t n, int k, int w, int mode) {
-  if (mode != SWS_MINI_HASH || k < 1 || k > 16 || w < 4 || w > KMAXW || n < (uint64_t)k + 32) return false;
+  if (mode != SWS_MINI_HASH || k < 1 || k > 29 || w < 4 || w > KMAXW || n < (uint64_t)k + 32) return false;
   const uint64_t m = n - (uint64_t)k + 1;
   return m <= (1ull << 32) - (1ull << 14) && (uint64_t)w <= m;
 }
@@ -102,7 +102,7 @@ cudaError_t launch_dna_min(const DnaMinArgs &d, void *ws, int *err, int num_sms,
   a.seq = d.seq;
   a.nbytes = (d.n + 3) / 4;
   a.k = (uint32_t)d.k;
-  a.kmask = 0xFFFFFFFFu >> (32 - 2 * d.k);
+  a.kmask = d.k <= 16 ? 0xFFFFFFFFu >> (32 - 2 * d.k) : 0u;
   a.m = (uint32_t)m;
   a.n_full = (uint32_t)m;
   a.nwin = (uint32_t)nwin;
@@ -110,6 +110,7 @@ cudaError_t launch_dna_min(const DnaMinArgs &d, void *ws, int *err, int num_sms,
   a.hdr = static_cast<KeysHeader *>(ws);
   a.status = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + 256);
   a.key_out = d.key_out;
+  a.key_out64 = d.key_out64;
   a.pos_out = d.pos_out;
   a.capacity = d.capacity;
   a.count_out = d.count_out;
@@ -135,6 +136,11 @@ cudaError_t launch_dna_min(const DnaMinArgs &d, void *ws, int *err, int num_sms,
       e = cudaMemsetAsync(tile_bar, 0, tiles * sizeof(uint2), st);
     if (e != cudaSuccess) return e;
     a.tile_bar = tile_bar;
+  }
+  if (d.k > 16) {  // 64-bit keys
+    if (kb == KB_NBLOCK) return launch_dna64_nblock(a, d.w, num_sms, st);
+    if (kb == KB_READS) return launch_dna64_reads(a, d.w, num_sms, st);
+    return launch_dna64_none(a, d.w, num_sms, st);
   }
   if (kb == KB_NBLOCK) return launch_dna_nblock(a, d.w, num_sms, st);
   if (kb == KB_READS) return launch_dna_reads(a, d.w, num_sms, st);

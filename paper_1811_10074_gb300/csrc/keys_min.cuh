@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda.h>
 
@@ -37,6 +38,14 @@ constexpr int KBMAX = 128;  // barriers of a tile kept in shared memory (more: r
 // read batches: a slot also keeps, per pick, the read it is the first pick of (or 0xFFFFFFFF)
 constexpr int KSLOT_BYTES_R = KCAP * 12;
 constexpr size_t KSMEM_DNA_R = 1024 + (size_t)KSLOTS * KSLOT_BYTES_R;
+// 64-bit keys (hashed k-mers with 16 < k <= 29): a key is (hash << 6) | (position + 1), position
+// -1 (code 0) being the k-mer before the thread's first, so the plain 64-bit minimum of a window
+// is its leftmost least key.  A slot holds KCAP64 picks: hashes, positions, and for read batches
+// the first-pick reads.
+constexpr int KCAP64 = 2048;
+__host__ __device__ constexpr int slot_bytes(bool k64, int kb) {
+  return k64 ? KCAP64 * (12 + (kb == KB_READS ? 4 : 0)) : (kb == KB_READS ? KSLOT_BYTES_R : KSLOT_BYTES);
+}
 constexpr uint32_t ST_DONE = 0x80000000u;  // status: count published (low bits)
 constexpr uint32_t ST_FAIL = 0xC0000000u;  // status: the tile failed
 constexpr uint32_t ST_COUNT = 0x3FFFFFFFu;
@@ -71,6 +80,7 @@ struct KeysArgs {
   uint32_t *status;    // one word per tile, zeroed before the launch
   KeysHeader *hdr;     // zeroed before the launch
   uint32_t *key_out;
+  unsigned long long *key_out64;  // 64-bit keys
   uint32_t *pos_out;
   uint64_t capacity;
   uint64_t *count_out;
@@ -109,6 +119,52 @@ __device__ __forceinline__ uint32_t dna_key(const KeysArgs &a, uint32_t p) {
   const uint32_t wi = p >> 4;
   const uint32_t v = __funnelshift_r(seq_word(a, wi), seq_word(a, wi + 1), 2 * (p & 15));  // bases p .. p+15
   return mini::key_value32(mini::kmer32(v, (int)a.k, a.kmask), SWS_MINI_HASH, a.kmask);
+}
+
+// Hash of the k-mer at position p for 16 < k <= 29 (~0 past the last k-mer), unpacked.
+__device__ __forceinline__ unsigned long long dna_key64(const KeysArgs &a, uint32_t p) {
+  if (p >= a.m) return ~0ull;
+  const uint32_t wi = p >> 4, sh = 2 * (p & 15);
+  const uint32_t w0 = seq_word(a, wi), w1 = seq_word(a, wi + 1), w2 = seq_word(a, wi + 2);
+  const unsigned long long x = ((unsigned long long)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
+  const unsigned long long kmask = (1ull << (2 * a.k)) - 1ull;
+  return mini::key_value64_wide(mini::kmer64(x, (int)a.k, kmask), SWS_MINI_HASH, (uint32_t)(kmask >> 32));
+}
+
+// Minimum of every window j = 0..15 of a thread over distinct 64-bit keys (position in the low
+// bits), by the same blocks of W: no tie to break.
+template <int W>
+__device__ __forceinline__ void window_minima64(const unsigned long long (&X)[32], unsigned long long (&mv)[KWPT]) {
+  constexpr int NK = KWPT + W - 1;
+  unsigned long long S[KWPT], P[NK];
+#pragma unroll
+  for (int b = 0; b * W < KWPT; ++b) {
+    const int lo = b * W, hi = b * W + W - 1;
+    unsigned long long v = X[hi];
+    if (hi < KWPT) S[hi] = v;
+#pragma unroll
+    for (int i = hi - 1; i >= lo; --i) {
+      v = X[i] < v ? X[i] : v;
+      if (i < KWPT) S[i] = v;
+    }
+  }
+#pragma unroll
+  for (int b = 1; b * W <= KWPT + W - 2; ++b) {
+    const int lo = b * W;
+    const int hi = lo + W - 2 < NK - 1 ? lo + W - 2 : NK - 1;
+    unsigned long long v = X[lo];
+    P[lo] = v;
+#pragma unroll
+    for (int i = lo + 1; i <= hi; ++i) {
+      v = X[i] < v ? X[i] : v;
+      P[i] = v;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KWPT; ++j) {
+    if (j % W == 0) mv[j] = S[j];
+    else mv[j] = S[j] < P[j + W - 1] ? S[j] : P[j + W - 1];
+  }
 }
 
 // Minimum of every window j = 0..15 of a thread (keys X[j .. j+W-1]) and the thread-relative
@@ -251,41 +307,43 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
 // and round, so every warp store covers 128 consecutive bytes.  A slot holds tile-relative
 // positions, or read-local ones (read batches) with, after the KCAP picks, the read each pick is
 // the first pick of; that read's pick offset is the pick's output index.
-template <int KB>
+template <int KB, bool K64>
 __device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t cnt, uint32_t tile,
                                            unsigned long long base, const KeysArgs &a) {
-  const uint2 *sl = reinterpret_cast<const uint2 *>(slot);
-  const uint32_t *first = reinterpret_cast<const uint32_t *>(slot + KCAP * 8);
+  constexpr int CAP = K64 ? KCAP64 : KCAP;
+  const uint2 *sl = reinterpret_cast<const uint2 *>(slot);                     // 32-bit keys
+  const unsigned long long *sv = reinterpret_cast<const unsigned long long *>(slot);  // 64-bit keys
+  const uint32_t *sp = reinterpret_cast<const uint32_t *>(slot + CAP * 8);          // their positions
+  const uint32_t *first = reinterpret_cast<const uint32_t *>(slot + CAP * (K64 ? 12 : 8));
   const uint32_t pos0 = KB == KB_READS ? 0u : tile * (uint32_t)KTILE;
   if (KB == KB_READS)
     for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
       const uint32_t r = first[x];
       if (r != 0xFFFFFFFFu) a.pick_offsets[r] = base + x;
     }
-  if (base + cnt <= a.capacity) {
-    uint32_t *ko = a.key_out + base;
-    uint32_t *po = a.pos_out + base;
-    for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
-      const uint2 pk = sl[x];
-      ko[x] = pk.x;
-      po[x] = pos0 + pk.y;
-    }
-    return;
-  }
+  const bool all = base + cnt <= a.capacity;
   for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
     const unsigned long long gi = base + x;
-    if (gi < a.capacity) {
-      const uint2 pk = sl[x];
-      a.key_out[gi] = pk.x;
-      a.pos_out[gi] = pos0 + pk.y;
+    if (all || gi < a.capacity) {
+      if constexpr (K64) {
+        a.key_out64[gi] = sv[x];
+        a.pos_out[gi] = pos0 + sp[x];
+      } else {
+        const uint2 pk = sl[x];
+        a.key_out[gi] = pk.x;
+        a.pos_out[gi] = pos0 + pk.y;
+      }
     }
   }
 }
 
-template <int W, bool DNA, int KB>
+template <int W, bool DNA, int KB, bool K64 = false>
 __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUtensorMap tmap, KeysArgs a) {
   static_assert(KB == KB_NONE || DNA, "barriers belong to the DNA form");
-  constexpr int SLOTB = KB == KB_READS ? KSLOT_BYTES_R : KSLOT_BYTES;
+  static_assert(!K64 || DNA, "64-bit keys belong to the DNA form");
+  using V = std::conditional_t<K64, unsigned long long, uint32_t>;
+  constexpr int SLOTB = slot_bytes(K64, KB);
+  constexpr int CAP = K64 ? KCAP64 : KCAP;  // picks a slot holds
   extern __shared__ __align__(16) unsigned char ksm_raw[];
   // barriers of the tile of stage s in buffer s: (start, end) pairs and the index of the first and
   // their number.  Loaded one tile ahead, read before and after the tile's barrier, rewritten two
@@ -406,7 +464,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     const bool wok = __all_sync(kFull, ok);
     const uint32_t tb = tile * (uint32_t)KTILE;  // first window (and key) of the tile
     const uint32_t g0 = tb + (uint32_t)q0;      // this thread's first window
-    uint32_t mv[KWPT];
+    V mv[KWPT];
     int mp[KWPT];
     unsigned mask = 0;      // windows that store a pick
     unsigned firstm = 0;    // barriers: stored picks that open an N-free stretch or a read
@@ -417,9 +475,54 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     uint32_t r0 = 0, c1 = 0, c2 = 0;
     bool many = false;
     if (wok) {
-      uint32_t X[32];
-      uint32_t xm1;
-      if constexpr (DNA) {
+      V X[32];
+      V xm1;
+      if constexpr (K64) {
+        // 64-bit keys, (hash << 6) | (position + 1): k-mers g0 .. g0+15 from packed words g0/16 ..
+        // g0/16 + 2, reversed once; the halo and the k-mer before the warp as in the 32-bit form
+        const uint32_t wbase = g0 - (uint32_t)lane * KWPT;
+        uint32_t pe = 0xFFFFFFFFu;
+        if (lane < W - 1) pe = wbase + (uint32_t)(32 * KWPT + lane);
+        else if (lane == 31 && wbase > 0) pe = wbase - 1;
+        const unsigned long long extra = pe != 0xFFFFFFFFu ? dna_key64(a, pe) : ~0ull;  // unpacked
+        const unsigned long long kmask = (1ull << (2 * a.k)) - 1ull;
+        const uint32_t khi = (uint32_t)(kmask >> 32);
+        if (g0 + KWPT <= a.m && 4ull * ((g0 >> 4) + 3) <= a.nbytes) {
+          const uint32_t *sw = reinterpret_cast<const uint32_t *>(a.seq) + (g0 >> 4);
+          const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1), v2 = __ldg(sw + 2);
+          const uint32_t r2 = mini::rev_pairs32(v0), r1 = mini::rev_pairs32(v1), r0w = mini::rev_pairs32(v2);
+          const int fsh = 64 - 2 * (int)a.k;  // 6 .. 30 for 16 < k <= 29
+#pragma unroll
+          for (int j = 0; j < KWPT; ++j) {
+            const uint32_t lo = j == 0 ? r1 : __funnelshift_r(r0w, r1, 32 - 2 * j);  // bases j+31 .. j+16
+            const uint32_t hi = j == 0 ? r2 : __funnelshift_r(r1, r2, 32 - 2 * j);   // bases j+15 .. j
+            const unsigned long long fw = ((unsigned long long)(hi >> fsh) << 32) | __funnelshift_r(lo, hi, fsh);
+            const unsigned long long w64 =
+                ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) | __funnelshift_r(v0, v1, 2 * j);
+            const unsigned long long rc = ~w64 & kmask;
+            X[j] = (mini::wang_mix64_wide(fw < rc ? fw : rc, khi) << 6) | (unsigned long long)(j + 1);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < KWPT; ++j) {
+            const unsigned long long h = dna_key64(a, g0 + (uint32_t)j);
+            X[j] = h == ~0ull ? ~0ull : (h << 6) | (unsigned long long)(j + 1);
+          }
+        }
+        const unsigned long long ex31 = __shfl_sync(kFull, extra, 31);
+        xm1 = ex31 == ~0ull ? ~0ull : ex31 << 6;  // position -1: code 0
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (i < W - 1) {
+            const unsigned long long dn = __shfl_down_sync(kFull, X[i], 1);  // the next lane's, packed
+            const unsigned long long ex = __shfl_sync(kFull, extra, i);
+            const unsigned long long h = lane == 31 ? ex : (dn == ~0ull ? ~0ull : dn >> 6);
+            X[KWPT + i] = h == ~0ull ? ~0ull : (h << 6) | (unsigned long long)(KWPT + i + 1);
+          } else {
+            X[KWPT + i] = ~0ull;
+          }
+        }
+      } else if constexpr (DNA) {
         // keys of k-mers g0 .. g0+15 from packed words g0/16 and g0/16 + 1 (g0 is a multiple of 16);
         // the next thread's first W-1 keys by shuffle, lane 31's from the extra k-mers of lanes
         // 0 .. W-2 (the next warp's first W-1); lane 31's own extra k-mer is the one before the
@@ -490,14 +593,20 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           if (lane == 0 && g0 >= 1 && g0 - 1 >= a.n_full && g0 - 1 < a.m) xm1 = a.keys[g0 - 1];
         }
       }
-      window_minima<W>(X, mv, mp);
+      if constexpr (K64) {
+        window_minima64<W>(X, mv);
+#pragma unroll
+        for (int j = 0; j < KWPT; ++j) mp[j] = (int)(mv[j] & 63u) - 1;
+      } else {
+        window_minima<W>(X, mv, mp);
+      }
       // A window stores a pick when its pick (the position of its leftmost least key) differs
       // from the previous window's.  The window before this thread's first is the previous lane's
       // last (its position shifted to this thread's frame); lane 0 of each warp finds it from its
       // own keys: the k-mer before its first (position -1) and its first w - 1.
       int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
       if (lane == 0) {
-        uint32_t best = xm1;
+        V best = xm1;
         pp = -1;
 #pragma unroll
         for (int i = 0; i < W - 1; ++i)
@@ -622,7 +731,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     //      every tile in between (published two tiles ago or earlier) ----------------------------------
     if (pop) {
       const unsigned long long base = run_end + between;
-      write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+      write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
       if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
       run_tile = pt0;
       run_end = base + pc0;
@@ -631,14 +740,23 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       ps0 = ps1;
       --L;
     }
-    if (tot <= (uint32_t)KCAP) {
+    if (tot <= (uint32_t)CAP) {
       // ---- defer this tile: its picks wait in the next slot -----------------------------------------
       const int sl = (int)(pushes % KSLOTS);
       ++pushes;
-      uint2 *dst = reinterpret_cast<uint2 *>(slots + sl * SLOTB) + (woff + inc - cnt);
+      unsigned char *slotp = slots + sl * SLOTB;
+      uint32_t idx = woff + inc - cnt;  // this thread's first place in the slot
+      auto put = [&](uint32_t i, V v, uint32_t posf) {
+        if constexpr (K64) {
+          reinterpret_cast<unsigned long long *>(slotp)[i] = v >> 6;
+          reinterpret_cast<uint32_t *>(slotp + CAP * 8)[i] = posf;
+        } else {
+          reinterpret_cast<uint2 *>(slotp)[i] = make_uint2(v, posf);
+        }
+      };
       if constexpr (KB == KB_READS) {
         // read-local positions, and the read whose first pick it is
-        uint32_t *fst = reinterpret_cast<uint32_t *>(slots + sl * SLOTB + KCAP * 8) + (woff + inc - cnt);
+        uint32_t *fst = reinterpret_cast<uint32_t *>(slotp + CAP * (K64 ? 12 : 8)) + idx;
         const uint2 tbr = s_bt[s];
         const bool in_smem = tbr.y <= (uint32_t)KBMAX;
         uint32_t qq = qstart;
@@ -655,9 +773,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
               rd = tbr.x + qq;  // read g_lo + qq starts where barrier qq - 1 is
               rs = (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
             }
-            *dst = make_uint2(mv[j], tb + (uint32_t)(q0 + mp[j]) - rs);
+            put(idx, mv[j], tb + (uint32_t)(q0 + mp[j]) - rs);
             *fst = (firstm >> j) & 1u ? rd : NONE;
-            ++dst;
+            ++idx;
             ++fst;
           }
         }
@@ -665,8 +783,8 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
 #pragma unroll
         for (int j = 0; j < KWPT; ++j) {
           if ((mask >> j) & 1u) {
-            *dst = make_uint2(mv[j], (uint32_t)(q0 + mp[j]));
-            ++dst;
+            put(idx, mv[j], (uint32_t)(q0 + mp[j]));
+            ++idx;
           }
         }
       }
@@ -691,7 +809,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           break;
         }
         const unsigned long long base = run_end + btw;
-        write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+        write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
         if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
         run_tile = pt0;
         run_end = base + pc0;
@@ -729,7 +847,8 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
                 if ((firstm >> j) & 1u) a.pick_offsets[rd] = r;
               }
               if (r < a.capacity) {
-                a.key_out[r] = mv[j];
+                if constexpr (K64) a.key_out64[r] = mv[j] >> 6;
+                else a.key_out[r] = mv[j];
                 a.pos_out[r] = pos;
               }
               ++r;
@@ -751,7 +870,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       break;
     }
     const unsigned long long base = run_end + btw;
-    write_slot<KB>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+    write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
     if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
     run_tile = pt0;
     run_end = base + pc0;
@@ -776,10 +895,10 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   }
 }
 
-template <int W, bool DNA, int KB>
+template <int W, bool DNA, int KB, bool K64 = false>
 cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms, cudaStream_t st) {
-  auto kern = k_keys_min<W, DNA, KB>;
-  constexpr size_t smem = !DNA ? KSMEM : KB == KB_READS ? KSMEM_DNA_R : KSMEM_DNA;
+  auto kern = k_keys_min<W, DNA, KB, K64>;
+  constexpr size_t smem = !DNA ? KSMEM : 1024 + (size_t)KSLOTS * slot_bytes(K64, KB);
   static int per_sm[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -804,6 +923,10 @@ cudaError_t launch_w_keys(const CUtensorMap &map, const KeysArgs &a, int num_sms
 cudaError_t launch_dna_none(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
 cudaError_t launch_dna_nblock(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
 cudaError_t launch_dna_reads(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
+// The same with 64-bit keys (16 < k <= 29; keys_min_dna64*.cu).
+cudaError_t launch_dna64_none(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
+cudaError_t launch_dna64_nblock(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
+cudaError_t launch_dna64_reads(const KeysArgs &a, int w, int num_sms, cudaStream_t st);
 
 }  // namespace keysmin
 }  // namespace sws

@@ -59,10 +59,10 @@ def test_batch_graph_replays_any_size(options):
 
 @pytest.mark.parametrize("options", ["default", "lookback"])
 def test_batch_wide_keys(options):
-    """k = 19 (38-bit hashes): the staged kernel on 64-bit values, or the look-back kernel."""
+    """k = 19 (38-bit hashes): the single pass on 64-bit keys, or the look-back kernel."""
     rng = np.random.default_rng(5)
     bt = B.Batch(max_reads=500, max_bases=200_000, k=19, w=10, options=options)
-    assert bt.path == {"default": 0, "lookback": 1}[options]
+    assert bt.path == {"default": 2, "lookback": 1}[options]
     for i in range(2):
         seq, offs = make_batch(rng, 400, 60, 400, 20 + i)
         check_run(bt, seq, offs, 19, 10)

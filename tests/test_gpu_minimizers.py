@@ -323,7 +323,7 @@ def test_generic_staged_path(k, w):
 @pytest.mark.parametrize("w", list(range(4, 18)))
 def test_dna_single_pass_kernel(w):
     rng = np.random.default_rng(3000 + w)
-    for k in (1, 2, 7, 15, 16):
+    for k in (1, 2, 7, 15, 16, 17, 19, 23, 29):  # 32-bit keys up to k = 16, 64-bit above
         span = k + w - 1
         for n in (k + 32, span + 4095, span + 4096, span + 4097, span + 3 * 4096 + 1, 2_000_003):
             seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
@@ -333,7 +333,7 @@ def test_dna_single_pass_kernel(w):
                         ("period 3", np.tile(np.array([0, 1, 3], np.uint8), n // 3 + 1)[:n]),
                         ("two letters", rng.integers(0, 2, size=n).astype(np.uint8))):
         seq = synth.pack_codes(torch.from_numpy(codes))
-        for k in (5, 16):
+        for k in (5, 16, 19):
             check_minimizers(seq, n, k, w, "hash")
     # a view starting one byte in (bases 4 .. n+3): not 4-byte aligned, so the staged kernel runs
     n = 50_000
@@ -357,7 +357,7 @@ def check_batch_single_pass(seq, offs, k, w):
 
 # Read batches on the single-pass kernel (hashed k-mers, k <= 16, 4 <= w <= 17): read starts act
 # as window barriers, positions are read-local, each read's first pick gives its pick offset.
-@pytest.mark.parametrize("k,w", [(15, 10), (16, 17), (5, 4), (11, 13)])
+@pytest.mark.parametrize("k,w", [(15, 10), (16, 17), (5, 4), (11, 13), (19, 10), (29, 4), (17, 17)])
 def test_batch_single_pass_kernel(k, w):
     rng = np.random.default_rng(k * 100 + w)
     span = k + w - 1
@@ -389,3 +389,4 @@ def test_nblocks_single_pass_kernel(w):
         seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
         iv = random_nblocks(n, rng, count, maxlen)
         check_minimizers(seq, n, 15, w, "hash", iv)
+        check_minimizers(seq, n, 19, w, "hash", iv)
