@@ -492,16 +492,22 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1), v2 = __ldg(sw + 2);
           const uint32_t r2 = mini::rev_pairs32(v0), r1 = mini::rev_pairs32(v1), r0w = mini::rev_pairs32(v2);
           const int fsh = 64 - 2 * (int)a.k;  // 6 .. 30 for 16 < k <= 29
+          // the hash state stays below 2^(2k): HB bounds its high word's bits (2k - 32)
+          auto keys16 = [&](auto hb) {
+            constexpr int HB = decltype(hb)::value;
 #pragma unroll
-          for (int j = 0; j < KWPT; ++j) {
-            const uint32_t lo = j == 0 ? r1 : __funnelshift_r(r0w, r1, 32 - 2 * j);  // bases j+31 .. j+16
-            const uint32_t hi = j == 0 ? r2 : __funnelshift_r(r1, r2, 32 - 2 * j);   // bases j+15 .. j
-            const unsigned long long fw = ((unsigned long long)(hi >> fsh) << 32) | __funnelshift_r(lo, hi, fsh);
-            const unsigned long long w64 =
-                ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) | __funnelshift_r(v0, v1, 2 * j);
-            const unsigned long long rc = ~w64 & kmask;
-            X[j] = (mini::wang_mix64_wide(fw < rc ? fw : rc, khi) << 6) | (unsigned long long)(j + 1);
-          }
+            for (int j = 0; j < KWPT; ++j) {
+              const uint32_t lo = j == 0 ? r1 : __funnelshift_r(r0w, r1, 32 - 2 * j);  // bases j+31 .. j+16
+              const uint32_t hi = j == 0 ? r2 : __funnelshift_r(r1, r2, 32 - 2 * j);   // bases j+15 .. j
+              const unsigned long long fw = ((unsigned long long)(hi >> fsh) << 32) | __funnelshift_r(lo, hi, fsh);
+              const unsigned long long w64 =
+                  ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) | __funnelshift_r(v0, v1, 2 * j);
+              const unsigned long long rc = ~w64 & kmask;
+              X[j] = (mini::wang_mix64_hb<HB>(fw < rc ? fw : rc, khi) << 6) | (unsigned long long)(j + 1);
+            }
+          };
+          if (a.k <= 23) keys16(std::integral_constant<int, 14>{});
+          else keys16(std::integral_constant<int, 26>{});
         } else {
 #pragma unroll
           for (int j = 0; j < KWPT; ++j) {
@@ -602,20 +608,14 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       }
       // A window stores a pick when its pick (the position of its leftmost least key) differs
       // from the previous window's.  The window before this thread's first is the previous lane's
-      // last (its position shifted to this thread's frame); lane 0 of each warp finds it from its
-      // own keys: the k-mer before its first (position -1) and its first w - 1.
-      int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
-      if (lane == 0) {
-        V best = xm1;
-        pp = -1;
-#pragma unroll
-        for (int i = 0; i < W - 1; ++i)
-          if (X[i] < best) {
-            best = X[i];
-            pp = i;
-          }
-      }
-      mask = (mp[0] != pp || g0 == 0) ? 1u : 0u;
+      // last (its position shifted to this thread's frame).  For lane 0 of a warp it is the key
+      // before the warp (position -1) with keys 0 .. w-2, and window 0 (keys 0 .. w-1) is one
+      // block of the combine: if its leftmost least key is key w-1 the two picks differ, else that
+      // key is also the leftmost least of keys 0 .. w-2 and the picks agree unless the key before
+      // is not larger.
+      const int pp = __shfl_up_sync(kFull, mp[KWPT - 1], 1) - KWPT;
+      const bool same0 = lane == 0 ? (mp[0] <= W - 2 && xm1 > mv[0]) : mp[0] == pp;
+      mask = (!same0 || g0 == 0) ? 1u : 0u;
 #pragma unroll
       for (int j = 1; j < KWPT; ++j) mask |= (unsigned)(mp[j] != mp[j - 1]) << j;
       const int left = (int)(a.nwin - g0);  // windows of this thread inside the sequence (if > 0)

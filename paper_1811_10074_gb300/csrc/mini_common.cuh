@@ -117,6 +117,27 @@ __device__ __forceinline__ unsigned long long wang_mix64_wide(unsigned long long
   x = mask(x * 0x80000001ull);
   return x;
 }
+// wang_mix64_wide when every value it forms stays below 2^(32 + HB) (2k = 32 + HB bits): a right
+// shift by s >= HB leaves nothing in the high word, so that xor-shift only changes the low word.
+template <int HB>
+__device__ __forceinline__ unsigned long long wang_mix64_hb(unsigned long long x, uint32_t mhi) {
+  auto mask = [mhi](unsigned long long v) {
+    return ((unsigned long long)((uint32_t)(v >> 32) & mhi) << 32) | (uint32_t)v;
+  };
+  auto xs = [](unsigned long long v, int s) {
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    if (HB <= s) return ((unsigned long long)hi << 32) | (lo ^ __funnelshift_r(lo, hi, s));
+    return v ^ (v >> s);
+  };
+  x = mask(x * 0x1FFFFFull + 0xFFFFFFFFFFFFFFFFull);
+  x = xs(x, 24);
+  x = mask(x * 265ull);
+  x = xs(x, 14);
+  x = mask(x * 21ull);
+  x = xs(x, 28);
+  x = mask(x * 0x80000001ull);
+  return x;
+}
 // Reverse the order of the 2-bit groups of a word.
 __device__ __forceinline__ uint32_t rev_pairs32(uint32_t x) {
   x = __brev(x);
