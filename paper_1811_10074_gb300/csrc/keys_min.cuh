@@ -306,20 +306,24 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
 // Copy a placed tile's picks from its slot to the output (keys, positions): one pick per thread
 // and round, so every warp store covers 128 consecutive bytes.  A slot holds tile-relative
 // positions, or read-local ones (read batches) with, after the KCAP picks, the read each pick is
-// the first pick of; that read's pick offset is the pick's output index.
+// the first pick of; that read's pick offset is the pick's output index.  The marker array is kept
+// all-empty between tiles: set only for first picks, and cleared here once read.
 template <int KB, bool K64>
-__device__ __forceinline__ void write_slot(const unsigned char *slot, uint32_t cnt, uint32_t tile,
+__device__ __forceinline__ void write_slot(unsigned char *slot, uint32_t cnt, uint32_t tile,
                                            unsigned long long base, const KeysArgs &a) {
   constexpr int CAP = K64 ? KCAP64 : KCAP;
   const uint2 *sl = reinterpret_cast<const uint2 *>(slot);                     // 32-bit keys
   const unsigned long long *sv = reinterpret_cast<const unsigned long long *>(slot);  // 64-bit keys
   const uint32_t *sp = reinterpret_cast<const uint32_t *>(slot + CAP * 8);          // their positions
-  const uint32_t *first = reinterpret_cast<const uint32_t *>(slot + CAP * (K64 ? 12 : 8));
+  uint32_t *first = reinterpret_cast<uint32_t *>(slot + CAP * (K64 ? 12 : 8));
   const uint32_t pos0 = KB == KB_READS ? 0u : tile * (uint32_t)KTILE;
   if (KB == KB_READS)
     for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
       const uint32_t r = first[x];
-      if (r != 0xFFFFFFFFu) a.pick_offsets[r] = base + x;
+      if (r != 0xFFFFFFFFu) {
+        a.pick_offsets[r] = base + x;
+        first[x] = 0xFFFFFFFFu;
+      }
     }
   const bool all = base + cnt <= a.capacity;
   for (uint32_t x = threadIdx.x; x < cnt; x += KNT) {
@@ -422,6 +426,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   // trip is not on the path of a refill
   const uint32_t first_dyn = (uint32_t)KSTAGES * gridDim.x;  // the first ticket handed out dynamically
   uint32_t spare = t == 0 ? first_dyn + atomicAdd(&a.hdr->ticket, 1u) : 0u;
+  if constexpr (KB == KB_READS)  // first-pick markers: empty
+    for (int i = t; i < KSLOTS * CAP; i += KNT)
+      reinterpret_cast<uint32_t *>(slots + (i / CAP) * SLOTB + CAP * (K64 ? 12 : 8))[i % CAP] = NONE;
   __syncthreads();
   if (KB != KB_NONE) {
     load_bars(s_tk[0], 0);
@@ -626,42 +633,50 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         // stores its pick (a new N-free stretch, or a new read)
         const uint2 tbr = s_bt[s];
         const uint32_t nb = tbr.y;
-        const bool in_smem = nb <= (uint32_t)KBMAX;
-        auto bst = [&](uint32_t i) -> long long { return in_smem ? s_bv[s][2 * i] : gstart(tbr.x + i); };
-        auto ben = [&](uint32_t i) -> long long { return in_smem ? s_bv[s][2 * i + 1] : gend(tbr.x + i); };
         const long long span = (long long)W + a.k - 1;
         const long long pf = (long long)g0 - 1;
-        uint32_t q = 0, hi = nb;
-        while (q < hi) {
-          const uint32_t mid = (q + hi) >> 1;
-          if (ben(mid) > pf) hi = mid;
-          else q = mid + 1;
-        }
-        qstart = q;
-        if constexpr (KB == KB_READS) {
-          r0 = (uint32_t)(q == 0 ? s_rs0[s] : bst(q - 1));
-          if (q < nb) {
-            c1 = (uint32_t)bst(q);
-            d1 = c1 - g0 < (uint32_t)KWPT ? (int)(c1 - g0) : KWPT;
+        // the list from shared memory, or (more than KBMAX barriers) from global memory: one
+        // uniform choice per tile, each accessor inlined into its own copy of the walk
+        auto walk = [&](auto bst, auto ben) -> unsigned {
+          uint32_t q = 0, hi = nb;
+          while (q < hi) {
+            const uint32_t mid = (q + hi) >> 1;
+            if (ben(mid) > pf) hi = mid;
+            else q = mid + 1;
           }
-          if (q + 1 < nb) {
-            c2 = (uint32_t)bst(q + 1);
-            d2 = c2 - g0 < (uint32_t)KWPT ? (int)(c2 - g0) : KWPT;
+          qstart = q;
+          if constexpr (KB == KB_READS) {
+            r0 = (uint32_t)(q == 0 ? s_rs0[s] : bst(q - 1));
+            if (q < nb) {
+              c1 = (uint32_t)bst(q);
+              d1 = c1 - g0 < (uint32_t)KWPT ? (int)(c1 - g0) : KWPT;
+            }
+            if (q + 1 < nb) {
+              c2 = (uint32_t)bst(q + 1);
+              d2 = c2 - g0 < (uint32_t)KWPT ? (int)(c2 - g0) : KWPT;
+            }
+            many = q + 2 < nb && bst(q + 2) - (long long)g0 < KWPT;
           }
-          many = q + 2 < nb && bst(q + 2) - (long long)g0 < KWPT;
-        }
-        // windows g0 - 1 .. g0 + 15 as bits 0 .. 16: barrier [bs, be) drops the windows
-        // [bs - span + 1, be - 1]; the barriers from q on, while they reach this thread's windows
-        unsigned v17 = (2u << KWPT) - 1u;
-        for (uint32_t qq = q; qq < nb; ++qq) {
-          const long long bs = bst(qq);
-          if (bs - span + 1 > (long long)g0 + KWPT - 1) break;  // it and every later one start beyond
-          const long long lo = bs - span + 1 - pf, hi2 = ben(qq) - 1 - pf;
-          if (hi2 >= 0) {
-            const int l = lo < 0 ? 0 : (int)lo, h = hi2 > KWPT ? KWPT : (int)hi2;
-            v17 &= ~(((2u << h) - 1u) & ~((1u << l) - 1u));
+          // windows g0 - 1 .. g0 + 15 as bits 0 .. 16: barrier [bs, be) drops the windows
+          // [bs - span + 1, be - 1]; the barriers from q on, while they reach this thread's windows
+          unsigned v = (2u << KWPT) - 1u;
+          for (uint32_t qq = q; qq < nb; ++qq) {
+            const long long bs = bst(qq);
+            if (bs - span + 1 > (long long)g0 + KWPT - 1) break;  // it and every later one start beyond
+            const long long lo = bs - span + 1 - pf, hi2 = ben(qq) - 1 - pf;
+            if (hi2 >= 0) {
+              const int l = lo < 0 ? 0 : (int)lo, h = hi2 > KWPT ? KWPT : (int)hi2;
+              v &= ~(((2u << h) - 1u) & ~((1u << l) - 1u));
+            }
           }
-        }
+          return v;
+        };
+        unsigned v17 =
+            nb <= (uint32_t)KBMAX
+                ? walk([&](uint32_t i) -> long long { return s_bv[s][2 * i]; },
+                       [&](uint32_t i) -> long long { return s_bv[s][2 * i + 1]; })
+                : walk([&](uint32_t i) -> long long { return gstart(tbr.x + i); },
+                       [&](uint32_t i) -> long long { return gend(tbr.x + i); });
         const long long lim = (long long)a.nwin - pf;  // bits of windows past the last are dropped
         if (lim <= 0) v17 = 0;
         else if (lim <= KWPT) v17 &= (1u << lim) - 1u;
@@ -755,28 +770,39 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         }
       };
       if constexpr (KB == KB_READS) {
-        // read-local positions, and the read whose first pick it is
-        uint32_t *fst = reinterpret_cast<uint32_t *>(slotp + CAP * (K64 ? 12 : 8)) + idx;
+        // read-local positions; a first pick of a read also marks that read in the slot's marker
+        // array (empty elsewhere)
+        uint32_t *fst = reinterpret_cast<uint32_t *>(slotp + CAP * (K64 ? 12 : 8));
         const uint2 tbr = s_bt[s];
-        const bool in_smem = tbr.y <= (uint32_t)KBMAX;
-        uint32_t qq = qstart;
+        if (!many) {
+          // at most two reads start among the windows: window j's read starts at r0, c1 or c2
+          const uint32_t pbq = tb + (uint32_t)q0;
+          const uint32_t pb0 = pbq - r0, pb1 = pbq - c1, pb2 = pbq - c2;
+          const uint32_t idx0 = idx;
 #pragma unroll
-        for (int j = 0; j < KWPT; ++j) {
-          if ((mask >> j) & 1u) {
-            uint32_t rd, rs;
-            if (!many) {
-              const int i = (j >= d1) + (j >= d2);
-              rd = tbr.x + qstart + (uint32_t)i;
-              rs = i == 0 ? r0 : i == 1 ? c1 : c2;
-            } else {
-              while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
-              rd = tbr.x + qq;  // read g_lo + qq starts where barrier qq - 1 is
-              rs = (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+          for (int j = 0; j < KWPT; ++j) {
+            if ((mask >> j) & 1u) {
+              const uint32_t pb = j >= d2 ? pb2 : (j >= d1 ? pb1 : pb0);
+              put(idx, mv[j], pb + (uint32_t)mp[j]);
+              ++idx;
             }
-            put(idx, mv[j], tb + (uint32_t)(q0 + mp[j]) - rs);
-            *fst = (firstm >> j) & 1u ? rd : NONE;
-            ++idx;
-            ++fst;
+          }
+          for (unsigned f = firstm; f; f &= f - 1u) {
+            const int j = __ffs(f) - 1;
+            fst[idx0 + __popc(mask & ((1u << j) - 1u))] = tbr.x + qstart + (uint32_t)((j >= d1) + (j >= d2));
+          }
+        } else {
+          const bool in_smem = tbr.y <= (uint32_t)KBMAX;
+          uint32_t qq = qstart;
+          for (int j = 0; j < KWPT; ++j) {
+            if ((mask >> j) & 1u) {
+              while (qq < tbr.y && (in_smem ? s_bv[s][2 * qq + 1] : gend(tbr.x + qq)) <= (long long)g0 + j) ++qq;
+              // read g_lo + qq starts where barrier qq - 1 is
+              const uint32_t rs = (uint32_t)(qq == 0 ? s_rs0[s] : (in_smem ? s_bv[s][2 * qq - 2] : gstart(tbr.x + qq - 1)));
+              put(idx, mv[j], tb + (uint32_t)(q0 + mp[j]) - rs);
+              if ((firstm >> j) & 1u) fst[idx] = tbr.x + qq;
+              ++idx;
+            }
           }
         }
       } else {

@@ -429,16 +429,46 @@ __global__ void k_fix_block_min(const uint64_t *__restrict__ po, uint64_t nreads
   if (threadIdx.x == 0) bmin[blockIdx.x] = s[0];
 }
 
-// Exclusive suffix minimum over the block minima, seeded with the total count.
-__global__ void k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks, const uint64_t *__restrict__ count,
-                           const unsigned long long *__restrict__ desc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Within a block of FIX_NT threads: the minimum of x over the threads after this one, and of
+// `carry`; tot (every thread) gets the minimum over all threads and carry.
+__device__ __forceinline__ uint64_t fix_suffix_after(uint64_t x, uint64_t carry, uint64_t *wsuf, uint64_t &tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {  // inclusive suffix minimum within the warp
+    const uint64_t u = __shfl_down_sync(0xFFFFFFFFu, x, d);
+    if (lane + d < 32) x = min(x, u);
+  }
+  if (lane == 0) wsuf[warp] = x;
+  __syncthreads();
+  uint64_t after = carry;
+  tot = carry;
+  for (int w2 = 0; w2 < FIX_NT / 32; ++w2) {
+    const uint64_t v = wsuf[w2];
+    tot = min(tot, v);
+    if (w2 > warp) after = min(after, v);
+  }
+  const uint64_t nxt = __shfl_down_sync(0xFFFFFFFFu, x, 1);
+  __syncthreads();  // wsuf may be rewritten by the caller's next round
+  return lane == 31 ? after : min(after, nxt);
+}
+
+// Exclusive suffix minimum over the block minima, seeded with the total count (one block; rounds
+// of FIX_NT block minima from the last).
+__global__ void __launch_bounds__(FIX_NT) k_fix_scan(uint64_t *__restrict__ bmin, uint64_t nblocks,
+                                                    const uint64_t *__restrict__ count,
+                                                    const unsigned long long *__restrict__ desc) {
+  __shared__ uint64_t wsuf[FIX_NT / 32];
   if (desc) nblocks = (desc[BD_NREADS] + FIX_BLOCK - 1) / FIX_BLOCK;
   uint64_t carry = *count;
-  for (uint64_t b = nblocks; b-- > 0;) {
-    const uint64_t v = bmin[b];
-    bmin[b] = carry;
-    carry = min(carry, v);
+  for (uint64_t hi = nblocks; hi > 0;) {
+    const uint64_t lo = hi > (uint64_t)FIX_NT ? hi - FIX_NT : 0;
+    const uint64_t b = lo + threadIdx.x;
+    const uint64_t v = b < hi ? bmin[b] : ~0ull;
+    uint64_t tot;
+    const uint64_t out = fix_suffix_after(v, carry, wsuf, tot);
+    if (b < hi) bmin[b] = out;
+    carry = tot;
+    hi = lo;
   }
 }
 
@@ -454,12 +484,20 @@ __global__ void k_fix_apply(uint64_t *__restrict__ po, uint64_t nreads, const ui
     s[j] = i < nreads ? po[i] : ~0ull;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t carry = nreads == 0 ? *count : carry_src[blockIdx.x];
-    for (int j = FIX_BLOCK - 1; j >= 0; --j) {
-      carry = min(carry, s[j]);
-      s[j] = carry;
-    }
+  {
+    // inclusive suffix minimum of s, seeded with the carry from the blocks after this one: each
+    // thread its FIX_PER consecutive entries, then across threads
+    const uint64_t carry = nreads == 0 ? *count : carry_src[blockIdx.x];
+    uint64_t e[FIX_PER];
+#pragma unroll
+    for (int j = 0; j < FIX_PER; ++j) e[j] = s[threadIdx.x * FIX_PER + j];
+#pragma unroll
+    for (int j = FIX_PER - 2; j >= 0; --j) e[j] = min(e[j], e[j + 1]);
+    __shared__ uint64_t wsuf[FIX_NT / 32];
+    uint64_t tot;
+    const uint64_t ex = fix_suffix_after(e[0], carry, wsuf, tot);
+#pragma unroll
+    for (int j = 0; j < FIX_PER; ++j) s[threadIdx.x * FIX_PER + j] = min(e[j], ex);
   }
   __syncthreads();
   for (int j = threadIdx.x; j < FIX_BLOCK; j += FIX_NT) {
@@ -558,7 +596,7 @@ cudaError_t launch_pick_offsets_fixup(uint64_t *po, uint64_t nreads, const uint6
     return cudaGetLastError();
   }
   k_fix_block_min<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, desc);
-  k_fix_scan<<<1, 32, 0, st>>>(scratch, nblocks, count, desc);
+  k_fix_scan<<<1, FIX_NT, 0, st>>>(scratch, nblocks, count, desc);
   k_fix_apply<<<(unsigned)nblocks, FIX_NT, 0, st>>>(po, nreads, scratch, count, desc);
   return cudaGetLastError();
 }
