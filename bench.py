@@ -57,7 +57,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (AUTO uses its fixed rule)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuners (AUTO uses its fixed rule; a read batch takes its default path)")
     ap.add_argument("--ops", default=",".join(OPS), help="comma list of operators to time")
     ap.add_argument("--ws", default=",".join(map(str, WS)), help="comma list of window sizes to time")
     ap.add_argument("--keys-n", type=int, default=1 << 28, help="keys of the --section keys measurement")
@@ -70,6 +71,8 @@ def parse_args():
     ap.add_argument("--genome-n", type=int, default=3_100_000_000, help="bases of the genome-scale table measurement")
     ap.add_argument("--table-hits", type=int, default=100_000_000, help="hits of the --section table-skew measurement")
     ap.add_argument("--fused", default="15,10", help="k,w of the --section fused measurement (--mini-n bases)")
+    ap.add_argument("--batch-plain", type=int, default=20_000,
+                    help="reads of the plain per-read comparison of --section batch (0: skip it)")
     args = ap.parse_args()
     args.ops = [o for o in args.ops.split(",") if o]
     args.ws = [int(v) for v in args.ws.split(",") if v]
@@ -649,10 +652,12 @@ def seeding_extras(seq, n, k, w, gh, gp, bucket_bits, ctx, stream, reps, n_reads
             "unit": "lookups_per_s and hits_per_s_m in millions per second"}
 
 
-def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain_sample: int = 20_000, reps: int = 5):
+def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain_sample: int = 20_000, reps: int = 5,
+                 tune: bool = True):
     """Batched reads: 1e6 short reads U[100,250] + 2e4 log-normal long reads (median 10 kb, max
-    200 kb), k=15 w=10, in one replayed graph (autotuned), against plain per-read launches through
-    the C ABI on a sample of reads with the same length distribution."""
+    200 kb), k=15 w=10, in one replayed graph (autotuned unless tune is off), against plain per-read
+    launches through the C ABI on a sample of reads with the same length distribution (none when
+    plain_sample is 0)."""
     import ctypes
     import paper_1811_10074_gb300 as P
     from paper_1811_10074_gb300 import binding as Bd
@@ -661,7 +666,7 @@ def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain
     lens = synth.read_lengths(n_short, n_long)
     packed, offs = synth.read_batch(lens, device=dev)
     total, nreads = int(offs[-1]), len(lens)
-    bt = P.Batch(nreads, total, 15, 10, options="tune", ctx=ctx)
+    bt = P.Batch(nreads, total, 15, 10, options="tune" if tune else "default", ctx=ctx)
     bt.load(packed, torch.from_numpy(offs).to(dev))
     bt.run(nreads, total)
     _, _, _ = bt.results()
@@ -680,6 +685,9 @@ def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain
                "tuned_ms": [round(v, 3) for v in bt.tuned_ms], "graph": True}
     bt.close()
     del packed
+    workload = "1e6 reads U[100,250] + 2e4 reads ln L ~ N(ln 1e4, 1), L <= 2e5; uniform ACGT; k=15 w=10"
+    if plain_sample <= 0:
+        return {"workload": workload, "batched_graph": batched}
     # plain: one sws_minimizers call per read, each read packed from a 16-byte boundary
     rng = np.random.default_rng(7)
     idx = np.sort(rng.choice(nreads, size=min(plain_sample, nreads), replace=False))
@@ -714,7 +722,7 @@ def batch_extras(dev, ctx, n_short: int = 1_000_000, n_long: int = 20_000, plain
     pbases = int(slens.sum())
     plain_r = {"reads_timed": len(slens), "bases_timed": pbases, "us_per_read": round(pms * 1e3 / len(slens), 2),
                "gbp_s": round(pbases / (pms / 1e3) / 1e9, 3), "host_wall_s": round(wall, 3)}
-    return {"workload": "1e6 reads U[100,250] + 2e4 reads ln L ~ N(ln 1e4, 1), L <= 2e5; uniform ACGT; k=15 w=10",
+    return {"workload": workload,
             "batched_graph": batched, "plain_per_read_launches": plain_r,
             "speedup_batched_vs_plain": round(batched["gbp_s"] / max(plain_r["gbp_s"], 1e-9), 1)}
 
@@ -877,7 +885,8 @@ def main():
             elif args.section == "table-skew":
                 print(json.dumps({"table_skew": table_skew_extras(dev, ctx, args.table_hits)}), flush=True)
             elif args.section == "batch":
-                print(json.dumps({"batched_reads": batch_extras(dev, ctx)}), flush=True)
+                print(json.dumps({"batched_reads": batch_extras(dev, ctx, plain_sample=args.batch_plain,
+                                                                tune=not args.no_tune)}), flush=True)
             else:
                 print(json.dumps({"serving": serve_extras(ctx)}), flush=True)
         return

@@ -38,10 +38,11 @@ constexpr int KBMAX = 128;  // barriers of a tile kept in shared memory (more: r
 // read batches: a slot also keeps, per pick, the read it is the first pick of (or 0xFFFFFFFF)
 constexpr int KSLOT_BYTES_R = KCAP * 12;
 constexpr size_t KSMEM_DNA_R = 1024 + (size_t)KSLOTS * KSLOT_BYTES_R;
-// 64-bit keys (hashed k-mers with 16 < k <= 29): a key is (hash << 6) | (position + 1), position
-// -1 (code 0) being the k-mer before the thread's first, so the plain 64-bit minimum of a window
-// is its leftmost least key.  A slot holds KCAP64 picks: hashes, positions, and for read batches
-// the first-pick reads.
+// 64-bit keys (hashed k-mers with 16 < k <= 29): a key is (hash << cb) | code, the code being the
+// k-mer's position + 1 in the tile (cb = 13, k <= 25) or in the thread's frame (cb = 6), so that
+// position -1 of the frame has the least code and the plain 64-bit minimum of a window is its
+// leftmost least key.  A slot holds KCAP64 picks: the packed keys themselves (cb = 13, outside
+// read batches), else hashes and positions, and for read batches the first-pick reads.
 constexpr int KCAP64 = 2048;
 __host__ __device__ constexpr int slot_bytes(bool k64, int kb) {
   return k64 ? KCAP64 * (12 + (kb == KB_READS ? 4 : 0)) : (kb == KB_READS ? KSLOT_BYTES_R : KSLOT_BYTES);
@@ -310,7 +311,7 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
 // all-empty between tiles: set only for first picks, and cleared here once read.
 template <int KB, bool K64>
 __device__ __forceinline__ void write_slot(unsigned char *slot, uint32_t cnt, uint32_t tile,
-                                           unsigned long long base, const KeysArgs &a) {
+                                           unsigned long long base, const KeysArgs &a, bool packed = false) {
   constexpr int CAP = K64 ? KCAP64 : KCAP;
   const uint2 *sl = reinterpret_cast<const uint2 *>(slot);                     // 32-bit keys
   const unsigned long long *sv = reinterpret_cast<const unsigned long long *>(slot);  // 64-bit keys
@@ -330,8 +331,14 @@ __device__ __forceinline__ void write_slot(unsigned char *slot, uint32_t cnt, ui
     const unsigned long long gi = base + x;
     if (all || gi < a.capacity) {
       if constexpr (K64) {
-        a.key_out64[gi] = sv[x];
-        a.pos_out[gi] = pos0 + sp[x];
+        const unsigned long long v = sv[x];
+        if (packed) {  // (hash << 13) | (tile position + 1)
+          a.key_out64[gi] = v >> 13;
+          a.pos_out[gi] = pos0 + ((uint32_t)v & 8191u) - 1u;
+        } else {
+          a.key_out64[gi] = v;
+          a.pos_out[gi] = pos0 + sp[x];
+        }
       } else {
         const uint2 pk = sl[x];
         a.key_out[gi] = pk.x;
@@ -377,6 +384,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   }
   const uint32_t T = a.num_tiles;
   constexpr uint32_t NONE = 0xFFFFFFFFu;
+  // 64-bit keys: code bits, and whether a slot keeps the packed keys themselves
+  const int cb = K64 && a.k <= 25 ? 13 : 6;
+  const bool pk = K64 && KB != KB_READS && cb == 13;
   // barrier i of the list: an N-block [start, end), or a read start (start = end), read i + 1
   auto gstart = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i] : a.bar[i + 1]; };
   auto gend = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i + 1] : a.bar[i + 1]; };
@@ -485,8 +495,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       V X[32];
       V xm1;
       if constexpr (K64) {
-        // 64-bit keys, (hash << 6) | (position + 1): k-mers g0 .. g0+15 from packed words g0/16 ..
-        // g0/16 + 2, reversed once; the halo and the k-mer before the warp as in the 32-bit form
+        // 64-bit keys, (hash << cb) | code: k-mers g0 .. g0+15 from packed words g0/16 .. g0/16 + 2,
+        // reversed once; the halo and the k-mer before the warp as in the 32-bit form
+        const uint32_t coff = cb == 13 ? (uint32_t)q0 : 0u;  // code of frame position p: coff + p + 1
         const uint32_t wbase = g0 - (uint32_t)lane * KWPT;
         uint32_t pe = 0xFFFFFFFFu;
         if (lane < W - 1) pe = wbase + (uint32_t)(32 * KWPT + lane);
@@ -499,9 +510,9 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1), v2 = __ldg(sw + 2);
           const uint32_t r2 = mini::rev_pairs32(v0), r1 = mini::rev_pairs32(v1), r0w = mini::rev_pairs32(v2);
           const int fsh = 64 - 2 * (int)a.k;  // 6 .. 30 for 16 < k <= 29
-          // the hash state stays below 2^(2k): HB bounds its high word's bits (2k - 32)
-          auto keys16 = [&](auto hb) {
-            constexpr int HB = decltype(hb)::value;
+          // the hash state stays below 2^(2k): HB bounds its high word's bits (2k - 32); CB = cb
+          auto keys16 = [&](auto hb, auto cbc) {
+            constexpr int HB = decltype(hb)::value, CB = decltype(cbc)::value;
 #pragma unroll
             for (int j = 0; j < KWPT; ++j) {
               const uint32_t lo = j == 0 ? r1 : __funnelshift_r(r0w, r1, 32 - 2 * j);  // bases j+31 .. j+16
@@ -510,27 +521,33 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
               const unsigned long long w64 =
                   ((unsigned long long)__funnelshift_r(v1, v2, 2 * j) << 32) | __funnelshift_r(v0, v1, 2 * j);
               const unsigned long long rc = ~w64 & kmask;
-              X[j] = (mini::wang_mix64_hb<HB>(fw < rc ? fw : rc, khi) << 6) | (unsigned long long)(j + 1);
+              X[j] = (mini::wang_mix64_hb<HB>(fw < rc ? fw : rc, khi) << CB) | (unsigned long long)(coff + j + 1);
             }
           };
-          if (a.k <= 23) keys16(std::integral_constant<int, 14>{});
-          else keys16(std::integral_constant<int, 26>{});
+          if (a.k <= 23) keys16(std::integral_constant<int, 14>{}, std::integral_constant<int, 13>{});
+          else if (a.k <= 25) keys16(std::integral_constant<int, 26>{}, std::integral_constant<int, 13>{});
+          else keys16(std::integral_constant<int, 26>{}, std::integral_constant<int, 6>{});
         } else {
 #pragma unroll
           for (int j = 0; j < KWPT; ++j) {
             const unsigned long long h = dna_key64(a, g0 + (uint32_t)j);
-            X[j] = h == ~0ull ? ~0ull : (h << 6) | (unsigned long long)(j + 1);
+            X[j] = h == ~0ull ? ~0ull : (h << cb) | (unsigned long long)(coff + j + 1);
           }
         }
         const unsigned long long ex31 = __shfl_sync(kFull, extra, 31);
-        xm1 = ex31 == ~0ull ? ~0ull : ex31 << 6;  // position -1: code 0
+        xm1 = ex31 == ~0ull ? ~0ull : (ex31 << cb) | (unsigned long long)coff;  // frame position -1
+        // the next lane's keys carry its frame's codes: the same in the tile (cb = 13), 16 less in
+        // a thread's frame (cb = 6: a valid key's low word is never all ones, the sentinel's is)
+        const uint32_t hoff = cb == 13 ? 0u : (uint32_t)KWPT;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           if (i < W - 1) {
-            const unsigned long long dn = __shfl_down_sync(kFull, X[i], 1);  // the next lane's, packed
+            const unsigned long long dn = __shfl_down_sync(kFull, X[i], 1);
             const unsigned long long ex = __shfl_sync(kFull, extra, i);
-            const unsigned long long h = lane == 31 ? ex : (dn == ~0ull ? ~0ull : dn >> 6);
-            X[KWPT + i] = h == ~0ull ? ~0ull : (h << 6) | (unsigned long long)(KWPT + i + 1);
+            const uint32_t dlo = (uint32_t)dn;
+            const unsigned long long nb =
+                ((dn >> 32) << 32) | (unsigned long long)(dlo == 0xFFFFFFFFu ? dlo : dlo + hoff);
+            X[KWPT + i] = lane == 31 ? (ex == ~0ull ? ~0ull : (ex << cb) | (unsigned long long)(coff + KWPT + i + 1)) : nb;
           } else {
             X[KWPT + i] = ~0ull;
           }
@@ -609,7 +626,8 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       if constexpr (K64) {
         window_minima64<W>(X, mv);
 #pragma unroll
-        for (int j = 0; j < KWPT; ++j) mp[j] = (int)(mv[j] & 63u) - 1;
+        for (int j = 0; j < KWPT; ++j)
+          mp[j] = (int)(((uint32_t)mv[j] & ((1u << cb) - 1u)) - (cb == 13 ? (uint32_t)q0 : 0u)) - 1;
       } else {
         window_minima<W>(X, mv, mp);
       }
@@ -746,7 +764,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     //      every tile in between (published two tiles ago or earlier) ----------------------------------
     if (pop) {
       const unsigned long long base = run_end + between;
-      write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+      write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
       if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
       run_tile = pt0;
       run_end = base + pc0;
@@ -763,7 +781,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       uint32_t idx = woff + inc - cnt;  // this thread's first place in the slot
       auto put = [&](uint32_t i, V v, uint32_t posf) {
         if constexpr (K64) {
-          reinterpret_cast<unsigned long long *>(slotp)[i] = v >> 6;
+          reinterpret_cast<unsigned long long *>(slotp)[i] = v >> cb;
           reinterpret_cast<uint32_t *>(slotp + CAP * 8)[i] = posf;
         } else {
           reinterpret_cast<uint2 *>(slotp)[i] = make_uint2(v, posf);
@@ -805,6 +823,15 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
             }
           }
         }
+      } else if (K64 && pk) {
+        // the packed keys carry their tile positions
+#pragma unroll
+        for (int j = 0; j < KWPT; ++j) {
+          if ((mask >> j) & 1u) {
+            reinterpret_cast<unsigned long long *>(slotp)[idx] = mv[j];
+            ++idx;
+          }
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < KWPT; ++j) {
@@ -835,7 +862,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           break;
         }
         const unsigned long long base = run_end + btw;
-        write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+        write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
         if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
         run_tile = pt0;
         run_end = base + pc0;
@@ -873,7 +900,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
                 if ((firstm >> j) & 1u) a.pick_offsets[rd] = r;
               }
               if (r < a.capacity) {
-                if constexpr (K64) a.key_out64[r] = mv[j] >> 6;
+                if constexpr (K64) a.key_out64[r] = mv[j] >> cb;
                 else a.key_out[r] = mv[j];
                 a.pos_out[r] = pos;
               }
@@ -896,7 +923,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       break;
     }
     const unsigned long long base = run_end + btw;
-    write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a);
+    write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
     if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
     run_tile = pt0;
     run_end = base + pc0;
