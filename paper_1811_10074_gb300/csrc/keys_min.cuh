@@ -534,24 +534,36 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
             X[j] = h == ~0ull ? ~0ull : (h << cb) | (unsigned long long)(coff + j + 1);
           }
         }
-        const unsigned long long ex31 = __shfl_sync(kFull, extra, 31);
-        xm1 = ex31 == ~0ull ? ~0ull : (ex31 << cb) | (unsigned long long)coff;  // frame position -1
+        // each lane's extra k-mer packed once, with the code it has where it is used: lanes 0 .. W-2
+        // hold lane 31's halo (frame positions KWPT + lane), lane 31 the k-mer before the warp
+        // (lane 0's frame position -1)
+        uint32_t ecode;
+        if (cb == 13) ecode = (wbase - tb) + (lane == 31 ? 0u : (uint32_t)(32 * KWPT + lane + 1));
+        else ecode = lane == 31 ? 0u : (uint32_t)(KWPT + lane + 1);
+        const unsigned long long extra_p = extra == ~0ull ? ~0ull : (extra << cb) | (unsigned long long)ecode;
+        xm1 = __shfl_sync(kFull, extra_p, 31);
         // the next lane's keys carry its frame's codes: the same in the tile (cb = 13), 16 less in
         // a thread's frame (cb = 6: a valid key's low word is never all ones, the sentinel's is)
-        const uint32_t hoff = cb == 13 ? 0u : (uint32_t)KWPT;
+        auto halo = [&](auto cbc) {
+          constexpr int CB = decltype(cbc)::value;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (i < W - 1) {
-            const unsigned long long dn = __shfl_down_sync(kFull, X[i], 1);
-            const unsigned long long ex = __shfl_sync(kFull, extra, i);
-            const uint32_t dlo = (uint32_t)dn;
-            const unsigned long long nb =
-                ((dn >> 32) << 32) | (unsigned long long)(dlo == 0xFFFFFFFFu ? dlo : dlo + hoff);
-            X[KWPT + i] = lane == 31 ? (ex == ~0ull ? ~0ull : (ex << cb) | (unsigned long long)(coff + KWPT + i + 1)) : nb;
-          } else {
-            X[KWPT + i] = ~0ull;
+          for (int i = 0; i < 16; ++i) {
+            if (i < W - 1) {
+              const unsigned long long dn = __shfl_down_sync(kFull, X[i], 1);
+              const unsigned long long ex = __shfl_sync(kFull, extra_p, i);
+              unsigned long long nb = dn;
+              if (CB == 6) {
+                const uint32_t dlo = (uint32_t)dn;
+                nb = ((dn >> 32) << 32) | (unsigned long long)(dlo == 0xFFFFFFFFu ? dlo : dlo + (uint32_t)KWPT);
+              }
+              X[KWPT + i] = lane == 31 ? ex : nb;
+            } else {
+              X[KWPT + i] = ~0ull;
+            }
           }
-        }
+        };
+        if (cb == 13) halo(std::integral_constant<int, 13>{});
+        else halo(std::integral_constant<int, 6>{});
       } else if constexpr (DNA) {
         // keys of k-mers g0 .. g0+15 from packed words g0/16 and g0/16 + 1 (g0 is a multiple of 16);
         // the next thread's first W-1 keys by shuffle, lane 31's from the extra k-mers of lanes
