@@ -311,7 +311,8 @@ __device__ __forceinline__ unsigned long long cta_counts(const uint32_t *status,
 // all-empty between tiles: set only for first picks, and cleared here once read.
 template <int KB, bool K64>
 __device__ __forceinline__ void write_slot(unsigned char *slot, uint32_t cnt, uint32_t tile,
-                                           unsigned long long base, const KeysArgs &a, bool packed = false) {
+                                           unsigned long long base, const KeysArgs &a, bool packed = false,
+                                           int vshift = 0) {
   constexpr int CAP = K64 ? KCAP64 : KCAP;
   const uint2 *sl = reinterpret_cast<const uint2 *>(slot);                     // 32-bit keys
   const unsigned long long *sv = reinterpret_cast<const unsigned long long *>(slot);  // 64-bit keys
@@ -341,7 +342,7 @@ __device__ __forceinline__ void write_slot(unsigned char *slot, uint32_t cnt, ui
         }
       } else {
         const uint2 pk = sl[x];
-        a.key_out[gi] = pk.x;
+        a.key_out[gi] = pk.x >> vshift;  // 32-bit DNA keys are held shifted left
         a.pos_out[gi] = pos0 + pk.y;
       }
     }
@@ -387,6 +388,8 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
   // 64-bit keys: code bits, and whether a slot keeps the packed keys themselves
   const int cb = K64 && a.k <= 25 ? 13 : 6;
   const bool pk = K64 && KB != KB_READS && cb == 13;
+  // 32-bit DNA keys are hashes shifted left by 32 - 2k (the same order), shifted back on output
+  const int ks = DNA && !K64 ? 32 - 2 * (int)a.k : 0;
   // barrier i of the list: an N-block [start, end), or a read start (start = end), read i + 1
   auto gstart = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i] : a.bar[i + 1]; };
   auto gend = [&](uint64_t i) -> long long { return KB == KB_NBLOCK ? a.bar[2 * i + 1] : a.bar[i + 1]; };
@@ -573,23 +576,28 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
         uint32_t pe = 0xFFFFFFFFu;
         if (lane < W - 1) pe = wbase + (uint32_t)(32 * KWPT + lane);
         else if (lane == 31 && wbase > 0) pe = wbase - 1;
-        const uint32_t extra = pe != 0xFFFFFFFFu ? dna_key(a, pe) : 0xFFFFFFFFu;
+        const uint32_t ex0 = pe != 0xFFFFFFFFu ? dna_key(a, pe) : 0xFFFFFFFFu;
+        const uint32_t extra = ex0 == 0xFFFFFFFFu ? ex0 : ex0 << ks;
         if (g0 + KWPT <= a.m && 4ull * ((g0 >> 4) + 2) <= a.nbytes) {
           const uint32_t *sw = reinterpret_cast<const uint32_t *>(a.seq) + (g0 >> 4);
           const uint32_t v0 = __ldg(sw), v1 = __ldg(sw + 1);
           // the 32 bases reversed once (base i at bits 62 - 2i of rhi:rlo): the forward k-mer at j
           // is then one funnel shift and one shift, with no per-k-mer reversal
           const uint32_t rhi = mini::rev_pairs32(v0), rlo = mini::rev_pairs32(v1);
-          const int fsh = 32 - 2 * (int)a.k;
+          const int fsh = 32 - 2 * (int)a.k;  // = ks
+          const uint32_t hm = 0xFFFFFFFFu << fsh;
 #pragma unroll
           for (int j = 0; j < KWPT; ++j) {
             const uint32_t rc = ~__funnelshift_r(v0, v1, 2 * j) & a.kmask;
             const uint32_t fw = (j == 0 ? rhi : __funnelshift_r(rlo, rhi, 32 - 2 * j)) >> fsh;
-            X[j] = mini::wang_mix32(fw < rc ? fw : rc, a.kmask);
+            X[j] = mini::wang_mix32_hi((fw < rc ? fw : rc) << fsh, hm);
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < KWPT; ++j) X[j] = dna_key(a, g0 + (uint32_t)j);
+          for (int j = 0; j < KWPT; ++j) {
+            const uint32_t h = dna_key(a, g0 + (uint32_t)j);
+            X[j] = h == 0xFFFFFFFFu ? h : h << ks;
+          }
         }
         xm1 = __shfl_sync(kFull, extra, 31);
 #pragma unroll
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
     //      every tile in between (published two tiles ago or earlier) ----------------------------------
     if (pop) {
       const unsigned long long base = run_end + between;
-      write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
+      write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk, ks);
       if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
       run_tile = pt0;
       run_end = base + pc0;
@@ -874,7 +882,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
           break;
         }
         const unsigned long long base = run_end + btw;
-        write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
+        write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk, ks);
         if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
         run_tile = pt0;
         run_end = base + pc0;
@@ -913,7 +921,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
               }
               if (r < a.capacity) {
                 if constexpr (K64) a.key_out64[r] = mv[j] >> cb;
-                else a.key_out[r] = mv[j];
+                else a.key_out[r] = mv[j] >> ks;
                 a.pos_out[r] = pos;
               }
               ++r;
@@ -935,7 +943,7 @@ __global__ void __launch_bounds__(KNT, 2) k_keys_min(const __grid_constant__ CUt
       break;
     }
     const unsigned long long base = run_end + btw;
-    write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk);
+    write_slot<KB, K64>(slots + ps0 * SLOTB, pc0, pt0, base, a, pk, ks);
     if (t == 0 && pt0 == T - 1) a.hdr->total = base + pc0;
     run_tile = pt0;
     run_end = base + pc0;

@@ -92,6 +92,20 @@ __device__ __forceinline__ uint32_t wang_mix32(uint32_t x, uint32_t m) {
   x = (x * 0x80000001u) & m;
   return x;
 }
+// wang_mix32 of x, computed on X = x << s (s = 32 - 2k, hm = 0xFFFFFFFF << s) and returned as
+// wang_mix32(x, 2^(2k) - 1) << s: arithmetic modulo 2^(2k) in the high 2k bits is plain 32-bit
+// arithmetic, so no multiply needs a mask; a right shift clears the low s bits it brings in.  The
+// additive constant -1 modulo 2^(2k), shifted, is hm itself.
+__device__ __forceinline__ uint32_t wang_mix32_hi(uint32_t X, uint32_t hm) {
+  X = X * 0x1FFFFFu + hm;
+  X ^= (X >> 24) & hm;
+  X *= 265u;
+  X ^= (X >> 14) & hm;
+  X *= 21u;
+  X ^= (X >> 28) & hm;
+  X *= 0x80000001u;
+  return X;
+}
 __device__ __forceinline__ unsigned long long wang_mix64(unsigned long long x, unsigned long long m) {
   x = (x * 0x1FFFFFull + 0xFFFFFFFFFFFFFFFFull) & m;
   x ^= x >> 24;
