@@ -316,14 +316,16 @@ def test_generic_staged_path(k, w):
     assert (to_u64(bh) == rh).all() and (bp.cpu().numpy().view(np.uint32) == rp).all()
 
 
-# The single-pass kernel on packed bases (hashed k-mers, k <= 16, 4 <= w <= 17, no N-blocks, the
-# sequence 4-byte aligned): each thread hashes 16 k-mers; a warp's halo k-mers are hashed by its
-# first w-1 lanes and its previous k-mer by lane 31.  Lengths around tiles of 4096 windows, ties
-# from low-complexity sequences, and an unaligned view that takes the staged path instead.
+# The single-pass kernel on packed bases (hashed k-mers, k <= 29, 4 <= w <= 17, the sequence
+# 4-byte aligned): each thread hashes 16 k-mers; a warp's halo k-mers are hashed by its first w-1
+# lanes and its previous k-mer by lane 31.  Lengths around tiles of 4096 windows, ties from
+# low-complexity sequences, and an unaligned view that takes the staged path instead.
 @pytest.mark.parametrize("w", list(range(4, 18)))
 def test_dna_single_pass_kernel(w):
     rng = np.random.default_rng(3000 + w)
-    for k in (1, 2, 7, 15, 16, 17, 19, 23, 29):  # 32-bit keys up to k = 16, 64-bit above
+    # 32-bit keys up to k = 16; 64-bit above, with tile position codes up to k = 25 (the hash's
+    # high word at most 14 bits up to k = 23, 26 bits above) and thread-frame codes from k = 26
+    for k in (1, 2, 7, 15, 16, 17, 19, 23, 25, 27, 29):
         span = k + w - 1
         for n in (k + 32, span + 4095, span + 4096, span + 4097, span + 3 * 4096 + 1, 2_000_003):
             seq = synth.acgt_uniform_packed(n, seed=int(rng.integers(1 << 30)))
